@@ -1,0 +1,363 @@
+/*
+ * sx.h -- C ABI of libsx, STREAM over execution targets on one B300 GPU (sm_103a).
+ *
+ * What the library does.  Heller, Kaiser, Diehl, Fey, Schweitzer, "Closing the Performance
+ * Gap with Modern C++", propose three ingredients for co-locating data and work: a *target*
+ * (an opaque handle to a place in the system, Section 3.1), an *allocator* that places arrays
+ * on a target and constructs them in bulk there (Section 3.2, Listing 1), and an *executor*
+ * that runs work on a target, with async_execute as its one required operation and
+ * execute / apply_execute / bulk_execute / bulk_async_execute derived from it (Section 3.3,
+ * Listing 2).  Parallel algorithms (copy, transform) then run on a vector placed on a target
+ * through a policy bound to an executor (Section 3.4, Listing 3).  The CUDA realisation makes a
+ * target a device number plus a stream, offloads bulk construction to the GPU and copies
+ * host<->device with CUDA memcpy (Section 4.2).  Section 5 (Listing 4) ports STREAM onto it:
+ * Copy c=a, Scale b=c*q, Add c=a+b, Triad a=b+c*q with q=3.0.
+ *
+ * This header is that design as a C ABI.  Plain pointers and sizes only; no C++ or torch
+ * types.  Every function returns an int status (SX_OK on success); no exception crosses the
+ * ABI.  On failure sx_last_error() returns a message for the calling thread.
+ *
+ * Arithmetic: every element operation is one IEEE-754 operation, round to nearest even, with
+ * no fused multiply-add and no flush-to-zero; Triad is two roundings (c*q, then b+that).
+ * Results are therefore bit-identical to a serial CPU loop in the same precision.  Generated
+ * NaNs (e.g. inf*0) have an unspecified sign and payload; copied NaNs keep their bits.
+ *
+ * Ownership: the caller owns every handle it creates and destroys it.  Destroy arrays,
+ * executors, futures, batches and servers before the target they were made on.  Memory the
+ * caller lends (sx_array_wrap, a borrowed stream) is never freed by the library.
+ *
+ * Threads: handles are not thread-safe unless stated (the server's submit/poll/wait/read/
+ * release are).  Distinct targets may be used from distinct threads.
+ */
+#ifndef SX_H_
+#define SX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------- */
+enum {
+    SX_OK = 0,
+    SX_ERR_INVALID = 1,   /* bad argument: NULL handle, size mismatch, bad config value     */
+    SX_ERR_OOM = 2,       /* target budget (host-side accounting) or device memory exhausted */
+    SX_ERR_DTYPE = 3,     /* operands of different or unsupported element types            */
+    SX_ERR_OVERLAP = 4,   /* output partially overlaps an input (exact aliasing is allowed)  */
+    SX_ERR_TIMEOUT = 5,   /* a host-side wait ran past its limit                             */
+    SX_ERR_CUDA = 6,      /* a CUDA runtime call failed; sx_last_error() carries its text    */
+    SX_ERR_NOT_READY = 7, /* non-blocking test: the work has not completed yet               */
+    SX_ERR_DEVICE = 8,    /* a kernel's bounded device-side wait expired; outputs invalid    */
+    SX_ERR_STATE = 9      /* the call is not valid in the object's current state            */
+};
+
+/* Message of the last failing call on this thread ("" if none).  Valid until the next call. */
+const char *sx_last_error(void);
+/* Static name of a status code ("SX_OK", "SX_ERR_OOM", ...). */
+const char *sx_status_string(int status);
+/* Library version, as major*10000 + minor*100 + patch. */
+int sx_version(void);
+
+/* ---- element types, operations, policies ------------------------------------------- */
+typedef enum sx_dtype { SX_F32 = 1, SX_F64 = 2, SX_U8 = 3 } sx_dtype;
+
+/* The four STREAM kernels (Section 5, Listing 4) with the library's operand convention:
+ *   COPY  out = x            SCALE out = x * q
+ *   ADD   out = x + y        TRIAD out = x + y * q
+ * SEED (batch/server items only) writes out[i] = the seeded uniform value of element
+ * (index_base + i), see sx_seed_uniform. */
+typedef enum sx_op {
+    SX_OP_COPY = 0, SX_OP_SCALE = 1, SX_OP_ADD = 2, SX_OP_TRIAD = 3, SX_OP_SEED = 4
+} sx_op;
+
+/* Execution policy bound to an executor (Section 3.4: par.on(exec); Listing 2's execute vs
+ * async_execute).  SX_PAR: the algorithm calls return after the work has completed on the
+ * device.  SX_PAR_TASK: they return once the work is enqueued on the target's stream; order
+ * follows the stream; completion is observed with futures or sx_executor_wait. */
+typedef enum sx_policy { SX_PAR = 1, SX_PAR_TASK = 2 } sx_policy;
+
+/* Kernel family.  VECTOR: grid-stride loop of 16- or 32-byte vector loads/stores per thread.
+ * BULK: a persistent kernel that stages tiles through shared memory with the Tensor Memory
+ * Accelerator's bulk copies (cp.async.bulk global->shared, compute, shared->global).
+ * AUTO: the autotuner's choice for (op, dtype, size) if it has one, else a fixed default. */
+typedef enum sx_variant { SX_VARIANT_AUTO = 0, SX_VARIANT_VECTOR = 1, SX_VARIANT_BULK = 2 } sx_variant;
+
+/* Launch configuration of one algorithm call.  A zero field means "default".
+ *   threads        threads per block (VECTOR: 128..1024, multiple of 32; BULK: 128..512)
+ *   blocks_per_sm  VECTOR: grid = SMs * blocks_per_sm with a grid-stride loop; 0 = one tile
+ *                  per block (grid covers the array).  BULK: persistent blocks per SM (1..2)
+ *   vec_bytes      VECTOR: 16 or 32 bytes per thread access
+ *   unroll         VECTOR: vector accesses per thread per tile (1, 2 or 4)
+ *   cache_hint     VECTOR: 0 = default caching, 1 = streaming (L1 no-allocate loads with an
+ *                  L2 256-byte prefetch hint, evict-first stores)
+ *   tile_bytes     BULK: bytes per array per pipeline stage (multiple of 1024, 4096..32768)
+ *   stages         BULK: pipeline depth (2..8); shared memory = stages*tile_bytes*inputs */
+typedef struct sx_launch_cfg {
+    int32_t variant;
+    int32_t threads;
+    int32_t blocks_per_sm;
+    int32_t vec_bytes;
+    int32_t unroll;
+    int32_t cache_hint;
+    int32_t tile_bytes;
+    int32_t stages;
+} sx_launch_cfg;
+
+/* ---- targets: Section 3.1 (a place in the system) and Section 4.2 (CUDA target =
+ *      device number + stream) ----------------------------------------------------------- */
+typedef struct sx_target sx_target;
+
+typedef struct sx_target_info {
+    int32_t device;          /* CUDA device ordinal                                      */
+    int32_t sm_count;        /* streaming multiprocessors                                 */
+    int32_t cc_major, cc_minor;
+    int64_t l2_bytes;        /* L2 cache size                                             */
+    int64_t hbm_total;       /* device memory, bytes                                      */
+    int64_t hbm_free;        /* free device memory at the time of the call                */
+    int64_t budget;          /* allocation budget of this target (bytes)                  */
+    int64_t used;            /* bytes currently allocated through this target             */
+    int32_t max_smem_block;  /* opt-in shared memory per block, bytes                     */
+    int32_t sm_clock_khz;    /* maximum SM clock                                          */
+    char name[128];          /* device name                                               */
+} sx_target_info;
+
+/* Number of visible CUDA devices (the paper's get_targets() for GPUs). */
+int sx_target_count(int *count);
+/* A target on `device` with its own non-blocking stream; budget = total device memory. */
+int sx_target_create(int device, sx_target **out);
+/* A target that borrows `stream` (a cudaStream_t; NULL = create an owned stream) and caps
+ * allocation through it at `budget_bytes` (0 = total device memory).  The stream must
+ * outlive the target. */
+int sx_target_create_ext(int device, void *stream, size_t budget_bytes, sx_target **out);
+int sx_target_destroy(sx_target *t);
+int sx_target_info_get(const sx_target *t, sx_target_info *out);
+/* The cudaStream_t the target enqueues on. */
+int sx_target_stream(const sx_target *t, void **stream);
+/* Wait for all work on the target's stream, then check the device error word that bounded
+ * device-side waits set (SX_ERR_DEVICE if one expired; the word is then cleared). */
+int sx_target_synchronize(sx_target *t);
+
+/* ---- arrays and the allocator: Section 3.2, Listing 1 (allocator_traits::target,
+ *      bulk_construct, bulk_destroy) and Section 4.2 (construction offloaded to the GPU) ---- */
+typedef struct sx_array sx_array;
+
+/* Allocate n elements of `dtype` on the target.  The data pointer is 256-byte aligned and
+ * followed by 256 guard bytes filled with 0xA5 (see sx_array_guard_ok).  The bytes are charged
+ * to the target's budget; if they do not fit, SX_ERR_OOM is returned without calling into the
+ * CUDA allocator.  Contents are undefined until constructed.  n = 0 is allowed. */
+int sx_alloc(sx_target *t, sx_dtype dtype, size_t n, sx_array **out);
+/* Borrow n elements of device memory at `device_ptr` (e.g. a torch tensor's storage).  Not
+ * charged to the budget, never freed.  Any alignment of the element type is accepted. */
+int sx_array_wrap(sx_target *t, sx_dtype dtype, void *device_ptr, size_t n, sx_array **out);
+/* Release an array (bulk_destroy is a no-op for these trivially destructible types). */
+int sx_free(sx_array *a);
+int sx_array_data(const sx_array *a, void **device_ptr, size_t *n, int *dtype);
+/* Owned arrays: *ok = 1 if the 256 guard bytes past the last element are untouched.  Waits
+ * for the target's stream first.  Borrowed arrays: *ok = 1. */
+int sx_array_guard_ok(const sx_array *a, int *ok);
+/* bulk_construct with one value: every element = (T)value.  Enqueued on the target stream. */
+int sx_bulk_construct(sx_array *a, double value);
+/* bulk_construct with seeded uniform values: element i = lo + (hi - lo) * u_i, evaluated in the
+ * array's type as RN(lo + RN(RN(hi - lo) * u_i)) with lo/hi first rounded to that type, where
+ * u_i = (w_i >> 11) * 2^-53 (F64) or (w_i >> 40) * 2^-24 (F32) and w_i is the (i+1)-th output
+ * of SplitMix64 (Steele, Lea & Flood 2014; Vigna's 64-bit finaliser) started from state
+ * `seed`.  Enqueued on the target stream. */
+int sx_seed_uniform(sx_array *a, uint64_t seed, double lo, double hi);
+
+/* ---- host<->device copy: Section 4.2 (copy specialised to CUDA memcpy) ---------------- */
+/* Copy n elements between host memory and the array, starting at element 0.  The blocking
+ * forms return once the copy has finished; the _async forms return once it is enqueued on the
+ * target's stream and need pinned (page-locked) host memory that stays valid until then. */
+int sx_copy_h2d(sx_array *dst, const void *host, size_t n);
+int sx_copy_d2h(void *host, const sx_array *src, size_t n);
+int sx_copy_h2d_async(sx_array *dst, const void *host, size_t n);
+int sx_copy_d2h_async(void *host, const sx_array *src, size_t n);
+
+/* ---- executors: Section 3.3, Listing 2 and Section 4.2 (CUDA executor) ---------------- */
+typedef struct sx_executor sx_executor;
+/* `cfg` NULL (or variant AUTO) lets each call pick its launch shape (autotuner table first,
+ * then the built-in default).  The executor keeps a copy of *cfg. */
+int sx_executor_create(sx_target *t, sx_policy policy, const sx_launch_cfg *cfg, sx_executor **out);
+int sx_executor_destroy(sx_executor *e);
+/* Block until all work enqueued on the executor's target has finished (then as
+ * sx_target_synchronize). */
+int sx_executor_wait(sx_executor *e);
+/* The launch configuration a call of (op, dtype, n) would use on this executor. */
+int sx_executor_resolve(const sx_executor *e, sx_op op, sx_dtype dtype, size_t n, sx_launch_cfg *out);
+
+/* ---- futures: async_execute's return value (Listing 2; Section 4.2 completes it from the
+ *      stream).  Backed by CUDA events, so they also give the device time of the work. ------- */
+typedef struct sx_future sx_future;
+/* SX_OK once complete, SX_ERR_TIMEOUT if timeout_ms (>= 0) elapsed first; < 0 waits forever.
+ * Also reports SX_ERR_DEVICE as sx_target_synchronize does. */
+int sx_future_wait(sx_future *f, int64_t timeout_ms);
+/* SX_OK if complete, SX_ERR_NOT_READY if not. */
+int sx_future_test(sx_future *f);
+/* Device time between the start and the end of the future's work (complete futures only). */
+int sx_future_elapsed_ms(sx_future *f, float *ms);
+int sx_future_destroy(sx_future *f);
+
+/* ---- parallel algorithms on placed arrays: Section 3.4 and Section 5, Listing 4 ------- */
+/* All arrays of one call must live on the executor's target, have the same element type
+ * (F32 or F64) and the same length.  `out` may be the same array as an input; a partial
+ * overlap is SX_ERR_OVERLAP.  n = 0 is a no-op.  q is converted to the element type once.
+ * The call follows the executor's policy (see sx_policy). */
+int sx_copy(sx_executor *e, const sx_array *src, sx_array *dst);                        /* dst = src       */
+int sx_transform_scale(sx_executor *e, const sx_array *in, sx_array *out, double q);    /* out = in * q    */
+int sx_transform_add(sx_executor *e, const sx_array *x, const sx_array *y, sx_array *out); /* out = x + y */
+int sx_transform_triad(sx_executor *e, const sx_array *x, const sx_array *y, sx_array *out,
+                       double q);                                                         /* out = x + y*q  */
+/* Any of the four by code (y ignored for COPY and SCALE; may be NULL). */
+int sx_execute(sx_executor *e, sx_op op, const sx_array *x, const sx_array *y, sx_array *out, double q);
+/* async_execute: always returns once enqueued.  If `fut` is not NULL a future is created for
+ * the work (the caller destroys it); NULL gives apply_execute's fire-and-forget. */
+int sx_execute_async(sx_executor *e, sx_op op, const sx_array *x, const sx_array *y,
+                     sx_array *out, double q, sx_future **fut);
+/* Listing 4's stream(): `iters` passes of Copy c=a, Scale b=c*q, Add c=a+b, Triad a=b+c*q,
+ * four launches per pass in stream order.  Follows the executor's policy. */
+int sx_stream_iter(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double q, int iters);
+/* The same `iters` passes computed by one kernel that reads a once and writes a, b, c once;
+ * bit-identical results (each element's chain of roundings is the same). */
+int sx_stream_fused(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double q, int iters);
+/* End to end from host memory: copy a, b, c (n elements, pinned or pageable host memory) to
+ * the target's arrays, run `iters` passes of sx_stream_iter, copy the three arrays back.
+ * Returns after the results are in host memory. */
+int sx_stream_host(sx_executor *e, void *host_a, void *host_b, void *host_c, sx_array *a,
+                   sx_array *b, sx_array *c, double q, int iters);
+
+/* Generic element transform with a device callable chosen from a registry (Section 3.4,
+ * Listing 3's transform(par.on(exec), s, to_upper); Section 4.2: any __device__ callable).
+ * Built-in callables for U8 arrays: SX_FN_TO_UPPER (ASCII a-z -> A-Z), SX_FN_TO_LOWER. */
+enum { SX_FN_TO_UPPER = 1, SX_FN_TO_LOWER = 2 };
+int sx_transform_u8(sx_executor *e, int fn, const sx_array *in, sx_array *out);
+
+/* ---- bulk execution over many independent instances (Listing 2's bulk_execute, one
+ *      persistent launch captured in a CUDA graph) -------------------------------------- */
+/* One instance: device pointers, all `n` elements long (72 bytes). */
+typedef struct sx_batch_item {
+    int32_t op;            /* sx_op (COPY..TRIAD, or SEED)                                */
+    int32_t dtype;         /* SX_F32 or SX_F64                                            */
+    uint64_t n;            /* elements                                                     */
+    const void *x;         /* first input (unused for SEED)                                */
+    const void *y;         /* second input (ADD, TRIAD; unused otherwise)                  */
+    void *out;             /* output                                                       */
+    double q;              /* scalar of SCALE and TRIAD; SEED: lo                          */
+    double q2;             /* SEED: hi                                                     */
+    uint64_t seed;         /* SEED: generator state (see sx_seed_uniform)                  */
+    uint64_t index_base;   /* SEED: generator index of out[0]                              */
+} sx_batch_item;
+
+/* Launch shape of a batch.  chunk_bytes: bytes moved per work tile (all arrays), the unit a
+ * block takes at a time (16 KiB..8 MiB); threads per block; blocks_per_sm of the persistent
+ * grid; vec_bytes 16/32.  Zero fields = default (autotuned values if sx_tune_batch ran). */
+typedef struct sx_batch_cfg {
+    int32_t chunk_bytes;
+    int32_t threads;
+    int32_t blocks_per_sm;
+    int32_t vec_bytes;
+} sx_batch_cfg;
+
+typedef struct sx_batch sx_batch;
+/* Build a batch: copies `items` into device memory, cuts every item into byte-balanced work
+ * tiles and captures the persistent kernel into a CUDA graph.  The items' pointers must stay
+ * valid while the batch is used.  Items must not write memory another item reads or writes. */
+int sx_batch_create(sx_target *t, const sx_batch_item *items, size_t count,
+                    const sx_batch_cfg *cfg, sx_batch **out);
+/* Run every item once: one graph launch on the target's stream (returns once enqueued). */
+int sx_batch_launch(sx_batch *b);
+/* Baseline: run every item with its own kernel launch, in order, on the same stream. */
+int sx_batch_launch_percall(sx_batch *b, const sx_launch_cfg *cfg);
+/* Completion times.  With recording on (sx_batch_set_record(b, 1), then a launch of either
+ * kind), sx_batch_completion_ns gives, after that launch has completed, each item's
+ * completion time in ns of the device global timer relative to the launch's first work. */
+int sx_batch_set_record(sx_batch *b, int record);
+int sx_batch_completion_ns(sx_batch *b, uint64_t *t_ns, size_t count);
+int sx_batch_info(const sx_batch *b, sx_batch_cfg *cfg, uint64_t *tiles, uint64_t *bytes);
+int sx_batch_destroy(sx_batch *b);
+
+/* ---- autotuner ------------------------------------------------------------------------ */
+/* Time the candidate launch shapes (both variants, vector widths, unroll, block counts,
+ * cache hints, bulk tile sizes) for (op, dtype, n) on scratch arrays the tuner allocates on the
+ * target, keep the fastest in the in-process table (keyed by device name, op, dtype and
+ * log2(n) bucket) and return it.  *gbs = its bandwidth (STREAM byte count). */
+int sx_tune(sx_target *t, sx_op op, sx_dtype dtype, size_t n, sx_launch_cfg *best, float *gbs);
+/* Tune the batch launch shape (chunk bytes, threads, blocks per SM, vector width) on `b`'s own
+ * items (outputs are overwritten), store it for batches with a similar item mix, rebuild `b`
+ * with it and return it.  *ms = device time of one launch with the best shape. */
+int sx_tune_batch(sx_batch *b, sx_batch_cfg *best, float *ms);
+/* Look up the table: SX_OK and *cfg if an entry covers (op, dtype, n), else SX_ERR_NOT_READY. */
+int sx_tune_lookup(const sx_target *t, sx_op op, sx_dtype dtype, size_t n, sx_launch_cfg *cfg);
+/* Persist / restore the table as JSON (entries for other devices are kept as they are). */
+int sx_tune_save(const char *path);
+int sx_tune_load(const char *path);
+int sx_tune_clear(void);
+
+/* ---- serving loop: continuous batching of STREAM requests on device-resident arrays ---- */
+typedef struct sx_server sx_server;
+
+enum { SX_SERVE_CONTINUOUS = 0, SX_SERVE_FIFO = 1 };
+typedef struct sx_server_cfg {
+    uint64_t budget_bytes;   /* device arena the server allocates once; admission bound    */
+    int32_t mode;            /* SX_SERVE_CONTINUOUS: each step runs a chunk of every active
+                                request in one launch; SX_SERVE_FIFO: one request at a time,
+                                one launch per phase, in arrival order (the per-call baseline) */
+    int32_t max_active;      /* requests admitted at once (slots), 1..4096                 */
+    int32_t chunk_bytes;     /* CONTINUOUS: bytes a request may move per step               */
+    int32_t steps_in_flight; /* CONTINUOUS: launched steps not yet completed (1..8)         */
+    int32_t threads, blocks_per_sm, vec_bytes, reserved;
+} sx_server_cfg;
+
+/* One request: construct its inputs on the device from seeds (x from seed_x, y from seed_y,
+ * uniform in [lo, hi)), then run `op` into `out`.  x, y and out live in the server's arena
+ * from admission until sx_server_release. */
+typedef struct sx_request {
+    int32_t op;      /* COPY..TRIAD */
+    int32_t dtype;   /* SX_F32 / SX_F64 */
+    uint64_t n;
+    double q;
+    uint64_t seed_x, seed_y;
+    double lo, hi;
+} sx_request;
+
+enum { SX_REQ_QUEUED = 0, SX_REQ_ACTIVE = 1, SX_REQ_DONE = 2, SX_REQ_REJECTED = 3,
+       SX_REQ_RELEASED = 4 };
+typedef struct sx_request_status {
+    int32_t state;        /* SX_REQ_*                                                      */
+    int32_t status;       /* SX_OK, or why it was rejected (SX_ERR_OOM: larger than arena)  */
+    double t_submit;      /* host monotonic seconds                                        */
+    double t_admit;
+    double t_done;        /* when the server saw its last step complete                    */
+    const void *x, *y;    /* device pointers (valid from admission to release)             */
+    void *out;
+} sx_request_status;
+
+typedef struct sx_server_stats {
+    uint64_t submitted, admitted, completed, rejected, steps, launches;
+    uint64_t bytes_moved;     /* STREAM byte count of completed work (seeding included)     */
+    uint64_t arena_used, arena_peak, arena_bytes;
+    double busy_seconds;      /* host time with at least one step in flight                 */
+} sx_server_stats;
+
+/* Start a server thread on the target (its stream carries every launch).  Thread-safe calls:
+ * submit, poll, wait, read, release, stats. */
+int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out);
+/* Queue a request; *id identifies it.  Requests larger than the arena are rejected at once
+ * (state REJECTED, status SX_ERR_OOM); others wait until slots and arena memory free up. */
+int sx_server_submit(sx_server *s, const sx_request *r, uint64_t *id);
+int sx_server_poll(sx_server *s, uint64_t id, sx_request_status *st);
+/* Wait until the request is DONE or REJECTED (SX_ERR_TIMEOUT after timeout_ms >= 0). */
+int sx_server_wait(sx_server *s, uint64_t id, int64_t timeout_ms, sx_request_status *st);
+/* Copy n elements of a DONE request's array (0 = x, 1 = y, 2 = out) to host memory. */
+int sx_server_read(sx_server *s, uint64_t id, int which, void *host, size_t n);
+/* Free a DONE (or REJECTED) request's arena memory. */
+int sx_server_release(sx_server *s, uint64_t id);
+int sx_server_stats_get(sx_server *s, sx_server_stats *st);
+/* Finish all admitted work, reject what is still queued, stop the thread, free the arena. */
+int sx_server_destroy(sx_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SX_H_ */

@@ -1,0 +1,38 @@
+"""STREAM over execution targets on one B300 GPU (Heller et al., "Closing the Performance Gap
+with Modern C++": targets, placing allocators, executors, and STREAM as parallel algorithms).
+
+The compute path is ``libsx.so`` (CUDA for sm_103a, C ABI in ``include/sx.h``); :mod:`.sx` is its
+ctypes binding with the header's names.  This module adds two torch conveniences: a target
+that enqueues on a torch stream, and wrapping a CUDA tensor's storage as a borrowed array.
+Importing fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+from . import sx
+from .sx import *  # noqa: F401,F403  (the header's names)
+
+__all__ = [n for n in dir(sx) if n.startswith(("sx_", "SX_"))] + [
+    "sx", "SxError", "target_on_torch_stream", "wrap_tensor", "dtype_of"]
+
+
+def dtype_of(tensor) -> int:
+    import torch
+    m = {torch.float32: sx.SX_F32, torch.float64: sx.SX_F64, torch.uint8: sx.SX_U8}
+    if tensor.dtype not in m:
+        raise TypeError(f"unsupported tensor dtype {tensor.dtype}")
+    return m[tensor.dtype]
+
+
+def target_on_torch_stream(device: int = 0, stream=None, budget_bytes: int = 0):
+    """A target on ``device`` that enqueues on ``stream`` (default: torch's current stream)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return sx.sx_target_create_ext(device, stream.cuda_stream, budget_bytes)
+
+
+def wrap_tensor(target, tensor):
+    """Borrow a contiguous CUDA tensor's elements as an ``sx_array`` (not charged, not freed)."""
+    if not tensor.is_cuda or not tensor.is_contiguous():
+        raise ValueError("wrap_tensor needs a contiguous CUDA tensor")
+    return sx.sx_array_wrap(target, dtype_of(tensor), tensor.data_ptr(), tensor.numel())

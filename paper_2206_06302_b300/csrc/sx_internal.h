@@ -1,0 +1,146 @@
+// sx_internal.h -- shared declarations of libsx's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "sx.h"
+
+namespace sx {
+
+// ---- errors --------------------------------------------------------------------------------
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+void clear_error();
+int cuda_fail(cudaError_t e, const char *what);
+
+#define SX_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::sx::cuda_fail(e_, #call);       \
+    } while (0)
+
+#define SX_TRY(call)                      \
+    do {                                  \
+        int s_ = (call);                  \
+        if (s_ != SX_OK) return s_;       \
+    } while (0)
+
+// Makes the target's device current for the scope of one API call.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline size_t dtype_size(int dt) {
+    switch (dt) {
+        case SX_F32: return 4;
+        case SX_F64: return 8;
+        case SX_U8: return 1;
+        default: return 0;
+    }
+}
+
+// Bytes one element of `op` moves (STREAM convention: every array read or written once).
+inline int op_arrays(int op) {
+    switch (op) {
+        case SX_OP_COPY: return 2;
+        case SX_OP_SCALE: return 2;
+        case SX_OP_ADD: return 3;
+        case SX_OP_TRIAD: return 3;
+        case SX_OP_SEED: return 1;
+        default: return 0;
+    }
+}
+
+}  // namespace sx
+
+// ---- handles -------------------------------------------------------------------------------
+struct sx_target {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t l2_bytes = 0;
+    size_t hbm_total = 0;
+    size_t budget = 0;
+    std::atomic<size_t> used{0};
+    int max_smem_block = 0;
+    int sm_clock_khz = 0;
+    std::string name;
+    // Device error word: kernels whose bounded waits expire write a non-zero code here.
+    int *d_err = nullptr;
+};
+
+struct sx_array {
+    sx_target *t = nullptr;
+    int dtype = 0;
+    size_t n = 0;
+    void *ptr = nullptr;
+    bool owned = false;
+    size_t alloc_bytes = 0;  // owned: data bytes rounded to 256 + 256 guard bytes
+    size_t data_bytes = 0;
+};
+
+struct sx_executor {
+    sx_target *t = nullptr;
+    int policy = SX_PAR;
+    bool fixed_cfg = false;
+    sx_launch_cfg cfg{};
+};
+
+struct sx_future {
+    sx_target *t = nullptr;
+    cudaEvent_t start = nullptr, end = nullptr;
+};
+
+namespace sx {
+
+constexpr int kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+
+// ---- kernels (sx_kernels.cu) ----------------------------------------------------------------
+// One STREAM kernel launch on `stream` with the resolved configuration `cfg` (variant VECTOR
+// or BULK).  x, y, out are element pointers; y may be null for COPY/SCALE.
+int launch_stream_op(const sx_target *t, cudaStream_t stream, int op, int dtype, const void *x,
+                     const void *y, void *out, size_t n, double q, const sx_launch_cfg &cfg);
+int launch_fill(cudaStream_t stream, int dtype, void *out, size_t n, double value);
+int launch_seed(cudaStream_t stream, int dtype, void *out, size_t n, uint64_t seed, double lo,
+                double hi, uint64_t index_base);
+int launch_stream_fused(const sx_target *t, cudaStream_t stream, int dtype, void *a, void *b,
+                        void *c, size_t n, double q, int iters);
+int launch_u8_transform(const sx_target *t, cudaStream_t stream, int fn, const void *in,
+                        void *out, size_t n);
+// TMA bulk-copy staging family (sx_bulk.cu).
+int launch_bulk_op(const sx_target *t, cudaStream_t stream, int op, int dtype, const void *x,
+                   const void *y, void *out, size_t n, double q, const sx_launch_cfg &cfg);
+int validate_bulk_cfg(const sx_target *t, int op, const sx_launch_cfg &cfg);
+// The configuration actually used for (op, dtype, n) when `req` leaves fields at 0.
+sx_launch_cfg resolve_cfg(const sx_target *t, int op, int dtype, size_t n, const sx_launch_cfg *req);
+// Checks a fully specified configuration; SX_ERR_INVALID with a message if unsupported.
+int validate_cfg(const sx_target *t, int op, const sx_launch_cfg &cfg);
+// Reads and clears the target's device error word.
+int check_device_error(const sx_target *t);
+
+// ---- autotuner table (sx_tune.cpp) ------------------------------------------------------
+bool tune_table_lookup(const sx_target *t, int op, int dtype, size_t n, sx_launch_cfg *cfg);
+bool tune_batch_lookup(const sx_target *t, double mean_item_bytes, sx_batch_cfg *cfg);
+void tune_batch_store(const sx_target *t, double mean_item_bytes, const sx_batch_cfg &cfg);
+
+// ---- monotonic host clock in seconds --------------------------------------------------------
+double now_seconds();
+
+}  // namespace sx

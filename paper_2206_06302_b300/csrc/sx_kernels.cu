@@ -1,0 +1,513 @@
+// sx_kernels.cu -- the STREAM element kernels (Section 5, Listing 4) for sm_103a.
+//
+// Copy c=a, Scale b=c*q, Add c=a+b, Triad a=b+c*q, with the library operand convention
+// COPY out=x, SCALE out=x*q, ADD out=x+y, TRIAD out=x+y*q.  Every arithmetic operation is
+// one IEEE operation rounded to nearest even through __dmul_rn/__dadd_rn/__fmul_rn/__fadd_rn,
+// which the compiler never fuses into a multiply-add; the library is also built with
+// -fmad=false and without fast-math (no flush-to-zero).  Results are therefore bit-identical
+// to a serial CPU loop.
+//
+// Nothing here is a contraction; the kernels are bound by HBM bandwidth.  The VECTOR family
+// moves 16 or 32 bytes per thread access (32-byte ld/st.global.v4.u64 are new with sm_100),
+// issues all loads of a tile before its stores so each thread keeps `unroll` vectors per
+// input in flight, and walks the array with a grid-stride loop or one tile per block.
+// The BULK family (sx_bulk.cu) stages tiles through shared memory with TMA bulk copies.
+#include "sx_internal.h"
+
+#include <cstdio>
+#include <type_traits>
+
+namespace sx {
+namespace {
+
+// ---- element arithmetic ------------------------------------------------------------------
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+template <int OP, class T>
+__device__ __forceinline__ T apply_op(T x, T y, T q) {
+    if constexpr (OP == SX_OP_COPY) return x;
+    else if constexpr (OP == SX_OP_SCALE) return mul_rn(x, q);
+    else if constexpr (OP == SX_OP_ADD) return add_rn(x, y);
+    else return add_rn(x, mul_rn(y, q));
+}
+
+// The op on one 64-bit word: one binary64 element or two binary32 elements.
+template <int OP, class T>
+__device__ __forceinline__ uint64_t op_word(uint64_t xw, uint64_t yw, T q) {
+    if constexpr (OP == SX_OP_COPY) {
+        return xw;
+    } else if constexpr (sizeof(T) == 8) {
+        double r = apply_op<OP, double>(__longlong_as_double((long long)xw),
+                                        __longlong_as_double((long long)yw), q);
+        return (uint64_t)__double_as_longlong(r);
+    } else {
+        float r0 = apply_op<OP, float>(__uint_as_float((uint32_t)xw), __uint_as_float((uint32_t)yw), q);
+        float r1 = apply_op<OP, float>(__uint_as_float((uint32_t)(xw >> 32)),
+                                       __uint_as_float((uint32_t)(yw >> 32)), q);
+        return (uint64_t)__float_as_uint(r0) | ((uint64_t)__float_as_uint(r1) << 32);
+    }
+}
+
+// ---- vector loads and stores (inline PTX) ---------------------------------------------------
+// HINT 0: read-only path (ld.global.nc), default stores.
+// HINT 1: streaming: read-only path without L1 allocation and a 256-byte L2 prefetch hint,
+//         evict-first (.cs) stores.
+// HINT 2: coherent loads (ld.global), used when the output aliases an input.
+template <int VB, int HINT>
+__device__ __forceinline__ void ldv(const char *p, uint64_t (&w)[VB / 8]) {
+    if constexpr (VB == 16) {
+        if constexpr (HINT == 0)
+            asm volatile("ld.global.nc.v2.u64 {%0,%1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(p));
+        else if constexpr (HINT == 1)
+            asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v2.u64 {%0,%1}, [%2];"
+                         : "=l"(w[0]), "=l"(w[1]) : "l"(p));
+        else
+            asm volatile("ld.global.v2.u64 {%0,%1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(p));
+    } else {
+        if constexpr (HINT == 0)
+            asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3]) : "l"(p));
+        else if constexpr (HINT == 1)
+            asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3]) : "l"(p));
+        else
+            asm volatile("ld.global.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3]) : "l"(p));
+    }
+}
+
+template <int VB, int HINT>
+__device__ __forceinline__ void stv(char *p, const uint64_t (&w)[VB / 8]) {
+    if constexpr (VB == 16) {
+        if constexpr (HINT == 1)
+            asm volatile("st.global.cs.v2.u64 [%0], {%1,%2};" ::"l"(p), "l"(w[0]), "l"(w[1]) : "memory");
+        else
+            asm volatile("st.global.v2.u64 [%0], {%1,%2};" ::"l"(p), "l"(w[0]), "l"(w[1]) : "memory");
+    } else {
+        if constexpr (HINT == 1)
+            asm volatile("st.global.cs.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(w[0]), "l"(w[1]),
+                         "l"(w[2]), "l"(w[3]) : "memory");
+        else
+            asm volatile("st.global.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(w[0]), "l"(w[1]),
+                         "l"(w[2]), "l"(w[3]) : "memory");
+    }
+}
+
+// ---- VECTOR kernel -------------------------------------------------------------------------
+// Elements [0, head) and [head + nvec*EPV, n) are done one by one by the first threads of the
+// grid; the body [head, head + nvec*EPV) is nvec vectors of VB bytes, all VB-aligned.
+template <int OP, class T, int VB, int U, int HINT>
+__global__ void __launch_bounds__(1024)
+k_stream_vec(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t nvec, T q) {
+    constexpr int W = VB / 8;
+    constexpr int EPV = VB / (int)sizeof(T);
+    constexpr bool HAS_Y = (OP == SX_OP_ADD || OP == SX_OP_TRIAD);
+
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t body_end = head + nvec * EPV;
+    if (gtid < head + (n - body_end)) {
+        const uint64_t i = gtid < head ? gtid : body_end + (gtid - head);
+        const T yv = HAS_Y ? y[i] : T(0);
+        out[i] = apply_op<OP, T>(x[i], yv, q);
+    }
+
+    const char *xb = reinterpret_cast<const char *>(x + head);
+    const char *yb = HAS_Y ? reinterpret_cast<const char *>(y + head) : nullptr;
+    char *ob = reinterpret_cast<char *>(out + head);
+    const uint64_t tile = (uint64_t)blockDim.x * U;
+    const uint64_t stride = (uint64_t)gridDim.x * tile;
+    for (uint64_t base = (uint64_t)blockIdx.x * tile; base < nvec; base += stride) {
+        uint64_t xw[U][W], yw[U][W];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t v = base + (uint64_t)u * blockDim.x + threadIdx.x;
+#pragma unroll
+            for (int k = 0; k < W; ++k) yw[u][k] = 0;
+            if (v < nvec) {
+                ldv<VB, HINT>(xb + v * VB, xw[u]);
+                if constexpr (HAS_Y) ldv<VB, HINT>(yb + v * VB, yw[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t v = base + (uint64_t)u * blockDim.x + threadIdx.x;
+            if (v < nvec) {
+                uint64_t r[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) r[k] = op_word<OP, T>(xw[u][k], yw[u][k], q);
+                stv<VB, HINT>(ob + v * VB, r);
+            }
+        }
+    }
+}
+
+// Element-by-element fallback when the arrays do not share an alignment modulo 16 bytes.
+template <int OP, class T>
+__global__ void __launch_bounds__(256) k_stream_scalar(const T *x, const T *y, T *out, uint64_t n, T q) {
+    constexpr bool HAS_Y = (OP == SX_OP_ADD || OP == SX_OP_TRIAD);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const T yv = HAS_Y ? y[i] : T(0);
+        out[i] = apply_op<OP, T>(x[i], yv, q);
+    }
+}
+
+template <int OP, class T, int VB, int U>
+cudaError_t launch_vec_hint(int hint, unsigned blocks, unsigned threads, cudaStream_t s, const T *x,
+                            const T *y, T *out, uint64_t n, uint64_t head, uint64_t nvec, T q) {
+    switch (hint) {
+        case 0: k_stream_vec<OP, T, VB, U, 0><<<blocks, threads, 0, s>>>(x, y, out, n, head, nvec, q); break;
+        case 1: k_stream_vec<OP, T, VB, U, 1><<<blocks, threads, 0, s>>>(x, y, out, n, head, nvec, q); break;
+        default: k_stream_vec<OP, T, VB, U, 2><<<blocks, threads, 0, s>>>(x, y, out, n, head, nvec, q); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int OP, class T, int VB>
+cudaError_t launch_vec_unroll(int unroll, int hint, unsigned blocks, unsigned threads, cudaStream_t s,
+                              const T *x, const T *y, T *out, uint64_t n, uint64_t head,
+                              uint64_t nvec, T q) {
+    switch (unroll) {
+        case 1: return launch_vec_hint<OP, T, VB, 1>(hint, blocks, threads, s, x, y, out, n, head, nvec, q);
+        case 2: return launch_vec_hint<OP, T, VB, 2>(hint, blocks, threads, s, x, y, out, n, head, nvec, q);
+        default: return launch_vec_hint<OP, T, VB, 4>(hint, blocks, threads, s, x, y, out, n, head, nvec, q);
+    }
+}
+
+bool ranges_overlap(const void *a, const void *b, size_t bytes) {
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    return pa < pb + bytes && pb < pa + bytes;
+}
+
+template <int OP, class T>
+int launch_vector(const sx_target *t, cudaStream_t s, const T *x, const T *y, T *out, size_t n, T q,
+                  const sx_launch_cfg &c) {
+    constexpr bool HAS_Y = (OP == SX_OP_ADD || OP == SX_OP_TRIAD);
+    const size_t bytes = n * sizeof(T);
+    int hint = c.cache_hint == 1 ? 1 : 0;
+    if (ranges_overlap(x, out, bytes) || (HAS_Y && ranges_overlap(y, out, bytes))) hint = 2;
+
+    const int VB = c.vec_bytes;
+    const uintptr_t mis = (uintptr_t)out % VB;
+    const bool same_mis = ((uintptr_t)x % VB == mis) && (!HAS_Y || (uintptr_t)y % VB == mis);
+    if (!same_mis || mis % sizeof(T) != 0) {
+        const unsigned threads = 256;
+        uint64_t blocks = (n + threads - 1) / threads;
+        const uint64_t cap = (uint64_t)t->sm_count * 8;
+        if (blocks > cap) blocks = cap;
+        if (blocks == 0) blocks = 1;
+        k_stream_scalar<OP, T><<<(unsigned)blocks, threads, 0, s>>>(x, y, out, n, q);
+        SX_CUDA(cudaGetLastError());
+        return SX_OK;
+    }
+    const size_t epv = VB / sizeof(T);
+    size_t head = ((VB - mis) % VB) / sizeof(T);
+    if (head > n) head = n;
+    const uint64_t nvec = (n - head) / epv;
+    const uint64_t nedge = n - nvec * epv;
+    const unsigned threads = (unsigned)c.threads;
+    const uint64_t tile = (uint64_t)threads * c.unroll;
+    uint64_t blocks = (nvec + tile - 1) / tile;
+    if (c.blocks_per_sm > 0) {
+        const uint64_t cap = (uint64_t)t->sm_count * c.blocks_per_sm;
+        if (blocks > cap) blocks = cap;
+    }
+    const uint64_t edge_blocks = (nedge + threads - 1) / threads;
+    if (blocks < edge_blocks) blocks = edge_blocks;
+    if (blocks == 0) blocks = 1;
+    if (blocks > 0x7fffffffull) return fail(SX_ERR_INVALID, "grid too large (%llu blocks)", (unsigned long long)blocks);
+    cudaError_t e;
+    if (VB == 16)
+        e = launch_vec_unroll<OP, T, 16>(c.unroll, hint, (unsigned)blocks, threads, s, x, y, out, n, head, nvec, q);
+    else
+        e = launch_vec_unroll<OP, T, 32>(c.unroll, hint, (unsigned)blocks, threads, s, x, y, out, n, head, nvec, q);
+    if (e != cudaSuccess) return cuda_fail(e, "k_stream_vec launch");
+    return SX_OK;
+}
+
+template <class T>
+int dispatch_op(const sx_target *t, cudaStream_t s, int op, const void *x, const void *y, void *out,
+                size_t n, double q, const sx_launch_cfg &c) {
+    const T *xt = static_cast<const T *>(x);
+    const T *yt = static_cast<const T *>(y);
+    T *ot = static_cast<T *>(out);
+    const T qt = (T)q;
+    switch (op) {
+        case SX_OP_COPY: return launch_vector<SX_OP_COPY, T>(t, s, xt, yt, ot, n, qt, c);
+        case SX_OP_SCALE: return launch_vector<SX_OP_SCALE, T>(t, s, xt, yt, ot, n, qt, c);
+        case SX_OP_ADD: return launch_vector<SX_OP_ADD, T>(t, s, xt, yt, ot, n, qt, c);
+        case SX_OP_TRIAD: return launch_vector<SX_OP_TRIAD, T>(t, s, xt, yt, ot, n, qt, c);
+        default: return fail(SX_ERR_INVALID, "unknown op %d", op);
+    }
+}
+
+// ---- seeded bulk construction (SplitMix64, counter form) ------------------------------------
+__device__ __forceinline__ uint64_t splitmix_word(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_seed_f64(double *out, uint64_t n, uint64_t seed, double lo, double span, uint64_t base) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = splitmix_word(seed, base + i);
+        const double u = __dmul_rn(__ull2double_rn(w >> 11), 0x1p-53);
+        out[i] = __dadd_rn(lo, __dmul_rn(span, u));
+    }
+}
+
+__global__ void k_seed_f32(float *out, uint64_t n, uint64_t seed, float lo, float span, uint64_t base) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = splitmix_word(seed, base + i);
+        const float u = __fmul_rn(__uint2float_rn((uint32_t)(w >> 40)), 0x1p-24f);
+        out[i] = __fadd_rn(lo, __fmul_rn(span, u));
+    }
+}
+
+template <class T>
+__global__ void k_fill(T *out, uint64_t n, T v) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = v;
+}
+
+unsigned setup_blocks(size_t n) {
+    uint64_t b = (n + 255) / 256;
+    if (b > 148ull * 16) b = 148ull * 16;
+    return b == 0 ? 1u : (unsigned)b;
+}
+
+// ---- fused STREAM passes ---------------------------------------------------------------------
+// Element i's chain of roundings over `iters` passes depends only on a[i]: Copy sets c=a,
+// Scale b=RN(c*q), Add c=RN(a+b), Triad a=RN(b+RN(c*q)).  One kernel can run the whole chain
+// per element from one read of a and write a, b, c once, bit-identical to four launches per
+// pass.
+template <class T>
+__device__ __forceinline__ void fused_chain(T &a, T &b, T &c, T q, int iters) {
+    for (int k = 0; k < iters; ++k) {
+        c = a;
+        b = mul_rn(c, q);
+        c = add_rn(a, b);
+        a = add_rn(b, mul_rn(c, q));
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_stream_fused(T *a, T *b, T *c, uint64_t n, T q, int iters) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        T av = a[i], bv, cv;
+        fused_chain(av, bv, cv, q, iters);
+        a[i] = av;
+        b[i] = bv;
+        c[i] = cv;
+    }
+}
+
+// 16-byte vector form of the fused kernel for arrays that are all 16-byte aligned.
+template <class T>
+__global__ void __launch_bounds__(256) k_stream_fused_v(T *a, T *b, T *c, uint64_t nvec, T q, int iters) {
+    constexpr int EPV = 16 / sizeof(T);
+    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        V av = reinterpret_cast<const V *>(a)[v];
+        T ae[EPV], be[EPV], ce[EPV];
+        memcpy(ae, &av, 16);
+#pragma unroll
+        for (int k = 0; k < EPV; ++k) fused_chain(ae[k], be[k], ce[k], q, iters);
+        V ao, bo, co;
+        memcpy(&ao, ae, 16);
+        memcpy(&bo, be, 16);
+        memcpy(&co, ce, 16);
+        reinterpret_cast<V *>(a)[v] = ao;
+        reinterpret_cast<V *>(b)[v] = bo;
+        reinterpret_cast<V *>(c)[v] = co;
+    }
+}
+
+// ---- generic byte transform: a registry of device callables (Listing 3's to_upper) ---------
+struct ToUpper {
+    __device__ __forceinline__ uint32_t operator()(uint32_t w) const {
+        // bytes in 'a'..'z' lose 0x20; SIMD-within-a-word compares give 0xff per true byte
+        const uint32_t m = __vcmpgeu4(w, 0x61616161u) & __vcmpleu4(w, 0x7a7a7a7au);
+        return w - (m & 0x20202020u);
+    }
+    __device__ __forceinline__ uint8_t operator()(uint8_t ch) const {
+        return (ch >= 'a' && ch <= 'z') ? (uint8_t)(ch - 0x20) : ch;
+    }
+};
+struct ToLower {
+    __device__ __forceinline__ uint32_t operator()(uint32_t w) const {
+        const uint32_t m = __vcmpgeu4(w, 0x41414141u) & __vcmpleu4(w, 0x5a5a5a5au);
+        return w + (m & 0x20202020u);
+    }
+    __device__ __forceinline__ uint8_t operator()(uint8_t ch) const {
+        return (ch >= 'A' && ch <= 'Z') ? (uint8_t)(ch + 0x20) : ch;
+    }
+};
+
+template <class F>
+__global__ void __launch_bounds__(256) k_u8_transform(const uint8_t *in, uint8_t *out, uint64_t n, uint64_t head, uint64_t nvec) {
+    F f;
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t body_end = head + nvec * 16;
+    if (gtid < head + (n - body_end)) {
+        const uint64_t i = gtid < head ? gtid : body_end + (gtid - head);
+        out[i] = f(in[i]);
+    }
+    const uint4 *vi = reinterpret_cast<const uint4 *>(in + head);
+    uint4 *vo = reinterpret_cast<uint4 *>(out + head);
+    for (uint64_t v = gtid; v < nvec; v += (uint64_t)gridDim.x * blockDim.x) {
+        uint4 w = vi[v];
+        w.x = f(w.x);
+        w.y = f(w.y);
+        w.z = f(w.z);
+        w.w = f(w.w);
+        vo[v] = w;
+    }
+}
+
+}  // namespace
+
+// ---- configuration -----------------------------------------------------------------------------
+sx_launch_cfg resolve_cfg(const sx_target *t, int op, int dtype, size_t n, const sx_launch_cfg *req) {
+    sx_launch_cfg c{};
+    if (req && req->variant != SX_VARIANT_AUTO) {
+        c = *req;
+    } else if (!tune_table_lookup(t, op, dtype, n, &c)) {
+        c = sx_launch_cfg{};
+        c.variant = SX_VARIANT_VECTOR;
+    }
+    if (c.variant == SX_VARIANT_VECTOR) {
+        if (c.threads == 0) c.threads = 256;
+        if (c.vec_bytes == 0) c.vec_bytes = 32;
+        if (c.unroll == 0) c.unroll = 2;
+    } else if (c.variant == SX_VARIANT_BULK) {
+        if (c.threads == 0) c.threads = 256;
+        if (c.blocks_per_sm == 0) c.blocks_per_sm = 1;
+        if (c.tile_bytes == 0) c.tile_bytes = 16384;
+        if (c.stages == 0) c.stages = 4;
+    }
+    return c;
+}
+
+int validate_cfg(const sx_target *t, int op, const sx_launch_cfg &c) {
+    if (c.variant == SX_VARIANT_VECTOR) {
+        if (c.threads < 32 || c.threads > 1024 || c.threads % 32)
+            return fail(SX_ERR_INVALID, "threads=%d: need a multiple of 32 in [32, 1024]", c.threads);
+        if (c.vec_bytes != 16 && c.vec_bytes != 32)
+            return fail(SX_ERR_INVALID, "vec_bytes=%d: need 16 or 32", c.vec_bytes);
+        if (c.unroll != 1 && c.unroll != 2 && c.unroll != 4)
+            return fail(SX_ERR_INVALID, "unroll=%d: need 1, 2 or 4", c.unroll);
+        if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64)
+            return fail(SX_ERR_INVALID, "blocks_per_sm=%d out of [0, 64]", c.blocks_per_sm);
+        if (c.cache_hint < 0 || c.cache_hint > 1)
+            return fail(SX_ERR_INVALID, "cache_hint=%d: need 0 or 1", c.cache_hint);
+        return SX_OK;
+    }
+    if (c.variant == SX_VARIANT_BULK) return validate_bulk_cfg(t, op, c);
+    return fail(SX_ERR_INVALID, "variant=%d: need VECTOR (1) or BULK (2)", c.variant);
+}
+
+int launch_stream_op(const sx_target *t, cudaStream_t s, int op, int dtype, const void *x, const void *y,
+                     void *out, size_t n, double q, const sx_launch_cfg &c) {
+    if (n == 0) return SX_OK;
+    if (c.variant == SX_VARIANT_BULK) return launch_bulk_op(t, s, op, dtype, x, y, out, n, q, c);
+    if (dtype == SX_F64) return dispatch_op<double>(t, s, op, x, y, out, n, q, c);
+    if (dtype == SX_F32) return dispatch_op<float>(t, s, op, x, y, out, n, q, c);
+    return fail(SX_ERR_DTYPE, "STREAM kernels take F32 or F64 (got dtype %d)", dtype);
+}
+
+int launch_fill(cudaStream_t s, int dtype, void *out, size_t n, double value) {
+    if (n == 0) return SX_OK;
+    const unsigned b = setup_blocks(n);
+    if (dtype == SX_F64) k_fill<double><<<b, 256, 0, s>>>((double *)out, n, value);
+    else if (dtype == SX_F32) k_fill<float><<<b, 256, 0, s>>>((float *)out, n, (float)value);
+    else if (dtype == SX_U8) k_fill<uint8_t><<<b, 256, 0, s>>>((uint8_t *)out, n, (uint8_t)value);
+    else return fail(SX_ERR_DTYPE, "bulk_construct: unsupported dtype %d", dtype);
+    SX_CUDA(cudaGetLastError());
+    return SX_OK;
+}
+
+int launch_seed(cudaStream_t s, int dtype, void *out, size_t n, uint64_t seed, double lo, double hi,
+                uint64_t index_base) {
+    if (n == 0) return SX_OK;
+    const unsigned b = setup_blocks(n);
+    if (dtype == SX_F64) {
+        const double span = hi - lo;
+        k_seed_f64<<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
+    } else if (dtype == SX_F32) {
+        const float lo32 = (float)lo, hi32 = (float)hi;
+        const float span = hi32 - lo32;
+        k_seed_f32<<<b, 256, 0, s>>>((float *)out, n, seed, lo32, span, index_base);
+    } else {
+        return fail(SX_ERR_DTYPE, "seed_uniform takes F32 or F64 (got dtype %d)", dtype);
+    }
+    SX_CUDA(cudaGetLastError());
+    return SX_OK;
+}
+
+int launch_stream_fused(const sx_target *t, cudaStream_t s, int dtype, void *a, void *b, void *c,
+                        size_t n, double q, int iters) {
+    if (n == 0 || iters <= 0) return SX_OK;
+    const size_t es = dtype_size(dtype);
+    const bool aligned = ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0) &&
+                         ((uintptr_t)c % 16 == 0) && ((n * es) % 16 == 0);
+    const uint64_t cap = (uint64_t)t->sm_count * 8;
+    if (aligned) {
+        const uint64_t nvec = n * es / 16;
+        uint64_t blocks = (nvec + 255) / 256;
+        if (blocks > cap) blocks = cap;
+        if (dtype == SX_F64)
+            k_stream_fused_v<double><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, nvec, q, iters);
+        else
+            k_stream_fused_v<float><<<(unsigned)blocks, 256, 0, s>>>((float *)a, (float *)b, (float *)c, nvec, (float)q, iters);
+    } else {
+        uint64_t blocks = (n + 255) / 256;
+        if (blocks > cap) blocks = cap;
+        if (dtype == SX_F64)
+            k_stream_fused<double><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, n, q, iters);
+        else
+            k_stream_fused<float><<<(unsigned)blocks, 256, 0, s>>>((float *)a, (float *)b, (float *)c, n, (float)q, iters);
+    }
+    SX_CUDA(cudaGetLastError());
+    return SX_OK;
+}
+
+int launch_u8_transform(const sx_target *t, cudaStream_t s, int fn, const void *in, void *out, size_t n) {
+    if (n == 0) return SX_OK;
+    const uintptr_t mis = (uintptr_t)out % 16;
+    uint64_t head, nvec;
+    if ((uintptr_t)in % 16 == mis) {
+        head = (16 - mis) % 16;
+        if (head > n) head = n;
+        nvec = (n - head) / 16;
+    } else {
+        head = n;  // everything one byte at a time
+        nvec = 0;
+    }
+    const uint64_t edge = n - nvec * 16;
+    uint64_t blocks = (nvec + 255) / 256;
+    const uint64_t cap = (uint64_t)t->sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    const uint64_t eb = (edge + 255) / 256;
+    if (blocks < eb) blocks = eb;
+    if (blocks == 0) blocks = 1;
+    if (blocks > 0x7fffffffull) return fail(SX_ERR_INVALID, "u8 transform: array too long for the byte path");
+    const uint8_t *ip = (const uint8_t *)in;
+    uint8_t *op = (uint8_t *)out;
+    if (fn == SX_FN_TO_UPPER) k_u8_transform<ToUpper><<<(unsigned)blocks, 256, 0, s>>>(ip, op, n, head, nvec);
+    else if (fn == SX_FN_TO_LOWER) k_u8_transform<ToLower><<<(unsigned)blocks, 256, 0, s>>>(ip, op, n, head, nvec);
+    else return fail(SX_ERR_INVALID, "unknown callable %d", fn);
+    SX_CUDA(cudaGetLastError());
+    return SX_OK;
+}
+
+}  // namespace sx

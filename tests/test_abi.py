@@ -1,0 +1,87 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every declared symbol, and
+host-side argument checking works without a GPU (no compute call is made)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sx.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sx_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_builds_and_loads():
+    from paper_2206_06302_b300 import build as b
+    path = b.build()
+    assert os.path.exists(path)
+    import paper_2206_06302_b300 as p
+    assert p.sx_version() == 10000
+
+
+def test_every_declared_symbol_is_exported():
+    from paper_2206_06302_b300 import build as b
+    path = b.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    assert len(declared_functions()) >= 60
+
+
+def test_binding_covers_the_header():
+    import paper_2206_06302_b300 as p
+    assert set(declared_functions()) == set(p.sx.EXPORTED)
+    for f in declared_functions():
+        assert hasattr(p.sx, f), f
+
+
+def test_status_strings():
+    import paper_2206_06302_b300 as p
+    assert p.sx_status_string(p.SX_OK) == "SX_OK"
+    assert p.sx_status_string(p.SX_ERR_OVERLAP) == "SX_ERR_OVERLAP"
+    assert p.sx_status_string(99) == "SX_ERR_UNKNOWN"
+
+
+def test_null_handles_are_rejected_without_a_gpu():
+    import paper_2206_06302_b300 as p
+    with pytest.raises(p.SxError) as ei:
+        p.sx_free(None)
+    assert ei.value.status == p.SX_ERR_INVALID
+    with pytest.raises(p.SxError) as ei:
+        p.sx_copy(None, None, None)
+    assert ei.value.status == p.SX_ERR_INVALID
+    with pytest.raises(p.SxError):
+        p.sx_tune_load("/nonexistent/table.json")
+
+
+def test_tune_table_roundtrip(tmp_path):
+    import paper_2206_06302_b300 as p
+    path = tmp_path / "t.json"
+    path.write_text('{"ops": [{"device": "X", "op": 3, "dtype": 2, "bucket": 27, "variant": 1,'
+                    ' "threads": 512, "blocks_per_sm": 0, "vec_bytes": 32, "unroll": 2,'
+                    ' "cache_hint": 1, "tile_bytes": 0, "stages": 0}],'
+                    ' "batch": [{"device": "X", "bucket": 20, "chunk_bytes": 262144,'
+                    ' "threads": 256, "blocks_per_sm": 4, "vec_bytes": 32}]}')
+    p.sx_tune_clear()
+    p.sx_tune_load(str(path))
+    out = tmp_path / "o.json"
+    p.sx_tune_save(str(out))
+    s = out.read_text()
+    assert '"threads": 512' in s and '"chunk_bytes": 262144' in s and '"device": "X"' in s
+    p.sx_tune_clear()
+
+
+def test_no_device_means_no_target():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2206_06302_b300 as p
+    with pytest.raises(p.SxError):
+        p.sx_target_create(0)

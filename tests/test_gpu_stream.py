@@ -1,0 +1,301 @@
+"""GPU parity of the STREAM kernels against the CPU oracle, through the C ABI.
+
+Bar: bit-for-bit equality (binary64 and binary32) on seeded inputs, for every kernel family and
+launch shape, at sizes that span several tiles with ragged heads and tails, misaligned and
+aliased operands, the hand-derived rounding cases, and STREAM's closed form.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2206_06302_b300 as sx
+import stream_inputs as si
+from gpu_util import assert_bitwise, bits, empty, to_device, to_host
+from test_oracle_pins import rounding_cases
+
+pytestmark = pytest.mark.gpu
+
+OPS = {"copy": sx.SX_OP_COPY, "scale": sx.SX_OP_SCALE, "add": sx.SX_OP_ADD,
+       "triad": sx.SX_OP_TRIAD}
+SIZES = [1, 2, 3, 5, 7, 8, 31, 33, 255, 257, 1000, 4099, 65537, (1 << 20) + 3]
+
+VECTOR_CFGS = [
+    None,  # executor default / tuner table
+    dict(variant=sx.SX_VARIANT_VECTOR, threads=256, vec_bytes=16, unroll=1),
+    dict(variant=sx.SX_VARIANT_VECTOR, threads=128, vec_bytes=32, unroll=4, blocks_per_sm=2),
+    dict(variant=sx.SX_VARIANT_VECTOR, threads=1024, vec_bytes=32, unroll=2, cache_hint=1),
+    dict(variant=sx.SX_VARIANT_VECTOR, threads=512, vec_bytes=16, unroll=4, blocks_per_sm=1,
+         cache_hint=1),
+]
+
+
+def _inputs(n, dt, salt=0):
+    x = si.uniform(si.array_seed(1000 + salt, 0, n), n, dt)
+    y = si.uniform(si.array_seed(1000 + salt, 1, n), n, dt)
+    return x, y
+
+
+def _run_op(target, cfg, op, x, y, q, dt):
+    e = sx.sx_executor_create(target, sx.SX_PAR, cfg)
+    try:
+        dx, dy, do = to_device(target, x), to_device(target, y), empty(target, dt, x.size)
+        try:
+            sx.sx_execute(e, OPS[op], dx, dy, do, q)
+            got = to_host(do)
+            assert sx.sx_array_guard_ok(do), "write past the end of the output"
+        finally:
+            for a in (dx, dy, do):
+                sx.sx_free(a)
+    finally:
+        sx.sx_executor_destroy(e)
+    return got
+
+
+@pytest.mark.parametrize("cfg", range(len(VECTOR_CFGS)))
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("op", list(OPS))
+def test_vector_parity_sizes(target, op, dt, cfg):
+    for n in SIZES:
+        x, y = _inputs(n, dt)
+        for q in (3.0, -0.1):
+            got = _run_op(target, VECTOR_CFGS[cfg], op, x, y, q, dt)
+            assert_bitwise(got, oracle.apply(op, x, y, q), f"{op} {dt.__name__} n={n} q={q}")
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_empty_arrays_are_noops(target, executor, dt):
+    a, b = empty(target, dt, 0), empty(target, dt, 0)
+    for op in OPS:
+        sx.sx_execute(executor, OPS[op], a, a, b, 3.0)
+    sx.sx_free(a)
+    sx.sx_free(b)
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("op", list(OPS))
+def test_misaligned_and_mixed_offsets(target, executor, op, dt):
+    """Borrowed arrays at element offsets: equal offsets take the vector path with scalar head
+    and tail; unequal offsets (modulo the vector width) take the element path."""
+    import torch
+    n = 70001
+    es = np.dtype(dt).itemsize
+    tdt = torch.float64 if dt == np.float64 else torch.float32
+    x, y = _inputs(n, dt, 7)
+    want = oracle.apply(op, x, y, 3.0)
+    for ox, oy, oo in [(1, 1, 1), (3, 3, 3), (0, 1, 2), (5, 0, 5), (2, 2, 0)]:
+        bx = torch.zeros(n + 8, dtype=tdt, device="cuda")
+        by = torch.zeros(n + 8, dtype=tdt, device="cuda")
+        bo = torch.full((n + 8,), -7.0, dtype=tdt, device="cuda")
+        bx[ox:ox + n] = torch.from_numpy(x).cuda()
+        by[oy:oy + n] = torch.from_numpy(y).cuda()
+        torch.cuda.synchronize()
+        ax = sx.sx_array_wrap(target, sx.SX_F64 if es == 8 else sx.SX_F32, bx.data_ptr() + ox * es, n)
+        ay = sx.sx_array_wrap(target, sx.SX_F64 if es == 8 else sx.SX_F32, by.data_ptr() + oy * es, n)
+        ao = sx.sx_array_wrap(target, sx.SX_F64 if es == 8 else sx.SX_F32, bo.data_ptr() + oo * es, n)
+        sx.sx_execute(executor, OPS[op], ax, ay, ao, 3.0)
+        out = bo.cpu().numpy()
+        assert_bitwise(out[oo:oo + n], want, f"{op} offsets {(ox, oy, oo)}")
+        assert np.all(out[:oo] == -7.0) and np.all(out[oo + n:] == -7.0), "wrote outside the range"
+        for a in (ax, ay, ao):
+            sx.sx_free(a)
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("op", list(OPS))
+def test_output_aliases_input(target, executor, op, dt):
+    n = 100003
+    x, y = _inputs(n, dt, 3)
+    want = oracle.apply(op, x, y, 3.0)
+    dx, dy = to_device(target, x), to_device(target, y)
+    sx.sx_execute(executor, OPS[op], dx, dy, dx, 3.0)  # out = x
+    assert_bitwise(to_host(dx), want, f"{op} out=x")
+    if op in ("add", "triad"):
+        dx2 = to_device(target, x)
+        sx.sx_execute(executor, OPS[op], dx2, dy, dy, 3.0)  # out = y
+        assert_bitwise(to_host(dy), want, f"{op} out=y")
+        sx.sx_free(dx2)
+    sx.sx_free(dx)
+    sx.sx_free(dy)
+
+
+def test_argument_errors(target, executor):
+    import torch
+    a = empty(target, np.float64, 100)
+    b = empty(target, np.float64, 101)
+    c = empty(target, np.float32, 100)
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_copy(executor, a, b)
+    assert ei.value.status == sx.SX_ERR_INVALID
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_copy(executor, a, c)
+    assert ei.value.status == sx.SX_ERR_DTYPE
+    buf = torch.zeros(200, dtype=torch.float64, device="cuda")
+    p1 = sx.sx_array_wrap(target, sx.SX_F64, buf.data_ptr(), 100)
+    p2 = sx.sx_array_wrap(target, sx.SX_F64, buf.data_ptr() + 8 * 50, 100)
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_copy(executor, p1, p2)
+    assert ei.value.status == sx.SX_ERR_OVERLAP
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_executor_create(target, sx.SX_PAR, dict(variant=sx.SX_VARIANT_VECTOR, threads=100))
+    assert ei.value.status == sx.SX_ERR_INVALID
+    u = empty(target, np.uint8, 100)
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_copy(executor, u, u)
+    assert ei.value.status == sx.SX_ERR_DTYPE
+    for h in (a, b, c, p1, p2, u):
+        sx.sx_free(h)
+
+
+def test_budget_is_enforced_on_the_host():
+    t = sx.sx_target_create_ext(0, None, 1 << 20)
+    a = sx.sx_alloc(t, sx.SX_F64, 1000)
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_alloc(t, sx.SX_F64, 1 << 20)
+    assert ei.value.status == sx.SX_ERR_OOM
+    info = sx.sx_target_info_get(t)
+    assert info["used"] == 8192 + 256 and info["budget"] == 1 << 20
+    sx.sx_free(a)
+    assert sx.sx_target_info_get(t)["used"] == 0
+    sx.sx_target_destroy(t)
+
+
+def test_rounding_cases_on_gpu(target, executor):
+    for dt, op, x, y, q, exp, note in rounding_cases():
+        n = 77
+        xa = np.full(n, x, dt)
+        ya = np.full(n, y if y is not None else 0, dt)
+        dx, dy, do = to_device(target, xa), to_device(target, ya), empty(target, dt, n)
+        sx.sx_execute(executor, OPS[op], dx, dy, do, q)
+        assert_bitwise(to_host(do), np.full(n, exp, dt), f"{op} {note}")
+        for a in (dx, dy, do):
+            sx.sx_free(a)
+
+
+def _stream_device(target, executor, a, b, c, q, iters, fused=False):
+    da, db, dc = to_device(target, a), to_device(target, b), to_device(target, c)
+    (sx.sx_stream_fused if fused else sx.sx_stream_iter)(executor, da, db, dc, q, iters)
+    out = tuple(to_host(h) for h in (da, db, dc))
+    for h in (da, db, dc):
+        sx.sx_free(h)
+    return out
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_closed_form_fp64_k10_config(target, executor, fused):
+    """STREAM FP64, n=2^20, a=1 b=2 c=0 q=3, 10 passes: the closed form, exactly."""
+    n = 1 << 20
+    a, b, c = si.closed_form_arrays(n, np.float64)
+    ga, gb, gc = _stream_device(target, executor, a, b, c, 3.0, 10, fused)
+    assert np.all(ga == 576650390625.0) and np.all(gb == 115330078125.0)
+    assert np.all(gc == 153773437500.0)
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_closed_form_fp32_k6(target, executor, fused):
+    n = 12345
+    a, b, c = si.closed_form_arrays(n, np.float32)
+    ga, gb, gc = _stream_device(target, executor, a, b, c, 3.0, 6, fused)
+    assert np.all(ga == 15.0 ** 6) and np.all(gb == 3 * 15.0 ** 5) and np.all(gc == 4 * 15.0 ** 5)
+
+
+@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_stream_passes_match_oracle(target, executor, dt, fused):
+    n = 65536 * 3 + 17
+    for iters in (1, 4, 40):
+        a, b, c = si.stream_arrays(n, dt, base_seed=77)
+        ga, gb, gc = _stream_device(target, executor, a, b, c, 3.0, iters, fused)
+        oracle.stream(a, b, c, 3.0, iters)
+        assert_bitwise(ga, a, f"a iters={iters}")
+        assert_bitwise(gb, b, f"b iters={iters}")
+        assert_bitwise(gc, c, f"c iters={iters}")
+
+
+def test_fused_equals_four_launches_unaligned(target, executor):
+    import torch
+    n = 50001
+    for dt, tdt, code in ((np.float64, torch.float64, sx.SX_F64), (np.float32, torch.float32, sx.SX_F32)):
+        a, b, c = si.stream_arrays(n, dt, base_seed=5)
+        oracle.stream(a, b, c, 3.0, 3)
+        buf = torch.from_numpy(np.concatenate([np.zeros(1, dt), si.stream_arrays(n, dt, base_seed=5)[0],
+                                               np.zeros(2 * n + 3, dt)])).cuda()
+        es = np.dtype(dt).itemsize
+        ha = sx.sx_array_wrap(target, code, buf.data_ptr() + es, n)
+        hb = sx.sx_array_wrap(target, code, buf.data_ptr() + es * (n + 1), n)
+        hc = sx.sx_array_wrap(target, code, buf.data_ptr() + es * (2 * n + 2), n)
+        sx.sx_stream_fused(executor, ha, hb, hc, 3.0, 3)
+        h = buf.cpu().numpy()
+        assert_bitwise(h[1:n + 1], a, "a")
+        assert_bitwise(h[n + 1:2 * n + 1], b, "b")
+        assert_bitwise(h[2 * n + 2:3 * n + 2], c, "c")
+        for x in (ha, hb, hc):
+            sx.sx_free(x)
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_seeded_construction_matches_generator(target, dt):
+    for n, seed, lo, hi in ((1, 0, -1.0, 1.0), (100003, 12345, -1.0, 1.0), (4097, 99, 0.25, 7.5),
+                            (300, 2 ** 63 + 5, -3.0, 0.1)):
+        d = empty(target, dt, n)
+        sx.sx_seed_uniform(d, seed, lo, hi)
+        assert_bitwise(to_host(d), si.uniform(seed, n, dt, lo, hi), f"seed {seed}")
+        sx.sx_free(d)
+
+
+def test_bulk_construct_fill(target):
+    for dt in (np.float64, np.float32, np.uint8):
+        d = empty(target, dt, 1001)
+        sx.sx_bulk_construct(d, 2.0)
+        assert np.all(to_host(d) == 2)
+        sx.sx_free(d)
+
+
+def test_to_upper_listing3(target, executor):
+    text = np.frombuffer(b"helloworld" + bytes(range(256)) * 41 + b"tail", np.uint8).copy()
+    for off in (0, 1, 5):
+        s = text[off:].copy()
+        ds, do = to_device(target, s), empty(target, np.uint8, s.size)
+        sx.sx_transform_u8(executor, sx.SX_FN_TO_UPPER, ds, do)
+        assert_bitwise(to_host(do), oracle.to_upper(s), "to_upper")
+        sx.sx_transform_u8(executor, sx.SX_FN_TO_LOWER, do, do)
+        assert to_host(do).tobytes() == s.tobytes().upper().lower()
+        sx.sx_free(ds)
+        sx.sx_free(do)
+
+
+def test_futures_async_execute(target):
+    e = sx.sx_executor_create(target, sx.SX_PAR_TASK)
+    n = 1 << 22
+    x, y = _inputs(n, np.float64, 11)
+    dx, dy, do = to_device(target, x), to_device(target, y), empty(target, np.float64, n)
+    f = sx.sx_execute_async(e, sx.SX_OP_TRIAD, dx, dy, do, 3.0)
+    sx.sx_future_wait(f, 10000)
+    assert sx.sx_future_test(f)
+    ms = sx.sx_future_elapsed_ms(f)
+    assert 0.0 < ms < 1000.0
+    sx.sx_future_destroy(f)
+    assert_bitwise(to_host(do), oracle.triad(x, y, 3.0))
+    # fire and forget, then wait on the executor
+    sx.sx_execute_async(e, sx.SX_OP_COPY, dx, None, do, 0.0, future=False)
+    sx.sx_executor_wait(e)
+    assert_bitwise(to_host(do), x)
+    for a in (dx, dy, do):
+        sx.sx_free(a)
+    sx.sx_executor_destroy(e)
+
+
+def test_stream_host_end_to_end(target, executor):
+    n = 300007
+    for dt in (np.float64, np.float32):
+        a, b, c = si.stream_arrays(n, dt, base_seed=21)
+        ha, hb, hc = a.copy(), b.copy(), c.copy()
+        da, db, dc = (empty(target, dt, n) for _ in range(3))
+        sx.sx_stream_host(executor, ha.ctypes.data, hb.ctypes.data, hc.ctypes.data, da, db, dc, 3.0, 3)
+        oracle.stream(a, b, c, 3.0, 3)
+        assert_bitwise(ha, a)
+        assert_bitwise(hb, b)
+        assert_bitwise(hc, c)
+        for h in (da, db, dc):
+            sx.sx_free(h)
