@@ -92,8 +92,14 @@ typedef enum sx_variant { SX_VARIANT_AUTO = 0, SX_VARIANT_VECTOR = 1, SX_VARIANT
  *   unroll         VECTOR: vector accesses per thread per tile (1, 2 or 4)
  *   cache_hint     VECTOR: 0 = default caching, 1 = streaming (L1 no-allocate loads with an
  *                  L2 256-byte prefetch hint, evict-first stores)
- *   tile_bytes     BULK: bytes per array per pipeline stage (multiple of 1024, 4096..32768)
- *   stages         BULK: pipeline depth (2..8); shared memory = stages*tile_bytes*inputs */
+ *   tile_bytes     BULK: bytes per array per pipeline stage (multiple of 1024, 1024..65536)
+ *   stages         BULK: pipeline depth (2..8); shared memory = stages*tile_bytes*inputs
+ *   fp64_mul       FP64 SCALE and TRIAD: where the product c*q is computed.  0 = the FP64
+ *                  pipe; 1 = the integer units (an exact round-to-nearest-even binary64 multiply
+ *                  that defers to the FP64 pipe for zero, subnormal, infinite and NaN operands
+ *                  and for subnormal or overflowing results); 2 = half of the elements each.
+ *                  All three give bit-identical results.  Ignored for FP32.
+ *   reserved       must be 0 */
 typedef struct sx_launch_cfg {
     int32_t variant;
     int32_t threads;
@@ -103,6 +109,8 @@ typedef struct sx_launch_cfg {
     int32_t cache_hint;
     int32_t tile_bytes;
     int32_t stages;
+    int32_t fp64_mul;
+    int32_t reserved;
 } sx_launch_cfg;
 
 /* ---- targets: Section 3.1 (a place in the system) and Section 4.2 (CUDA target =

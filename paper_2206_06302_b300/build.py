@@ -38,7 +38,8 @@ def _stale(obj: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
-    headers = [os.path.join(CSRC, "sx_internal.h"), os.path.join(INCLUDE, "sx.h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
+    headers.append(os.path.join(INCLUDE, "sx.h"))
     objs = []
     nvcc = _nvcc()
     for src in SOURCES:

@@ -1,17 +1,515 @@
-// sx_batch.cu -- placeholder until the persistent batched launcher is built.
+// sx_batch.cu -- bulk execution of many independent STREAM instances in one persistent launch
+// (Listing 2's bulk_execute over a shape of instances), captured once in a CUDA graph.
+//
+// The host cuts every item into work tiles of about `chunk_bytes` moved bytes (all of the item's
+// arrays counted), a multiple of 64 elements so that vector alignment is kept from tile to tile,
+// and lists the tiles item by item.  A persistent grid (SMs x blocks_per_sm) walks the list
+// round-robin: block b takes tiles b, b + grid, b + 2*grid, ...  Tiles are of equal bytes except
+// each item's last, so the static assignment balances the byte load without a work queue.
+// Inside a tile the block runs the same 16/32-byte vector loop as the VECTOR kernels, or an
+// element loop when the item's pointers do not share the vector alignment.
+//
+// Optional completion recording: after its last tile of an item, a block bumps the item's
+// counter; the block that completes the item writes %globaltimer.  The counters and stamps are
+// scratch memory of the batch, cleared by a memset node in the same graph before the kernel.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "sx_device.cuh"
 #include "sx_internal.h"
+
+namespace sx {
+namespace {
+
+using namespace dev;
+
+struct DevItem {
+    uint32_t op, dtype;
+    uint64_t n;
+    const void *x;
+    const void *y;
+    void *out;
+    double q, q2;
+    uint64_t seed, index_base;
+    uint32_t tile_elems, ntiles;
+};
+
+struct DevTile {
+    uint32_t item;
+    uint32_t index;  // tile index within the item
+};
+
+template <int OP, class T, int VB, int MM>
+__device__ __forceinline__ void tile_vector(const DevItem &it, uint64_t start, uint64_t cnt) {
+    constexpr int W = VB / 8;
+    constexpr int EPV = VB / (int)sizeof(T);
+    constexpr bool HY = has_y<OP>();
+    const T q = (T)it.q;
+    const T *x = static_cast<const T *>(it.x) + start;
+    const T *y = HY ? static_cast<const T *>(it.y) + start : nullptr;
+    T *o = static_cast<T *>(it.out) + start;
+    const uintptr_t mis = (uintptr_t)o % VB;
+    const bool vec_ok = ((uintptr_t)x % VB == mis) && (!HY || (uintptr_t)y % VB == mis) && mis % sizeof(T) == 0;
+    uint64_t head = 0, nvec = 0;
+    if (vec_ok) {
+        head = ((VB - mis) % VB) / sizeof(T);
+        if (head > cnt) head = cnt;
+        nvec = (cnt - head) / EPV;
+    } else {
+        head = cnt;
+    }
+    const uint64_t body_end = head + nvec * EPV;
+    for (uint64_t e = threadIdx.x; e < head + (cnt - body_end); e += blockDim.x) {
+        const uint64_t i = e < head ? e : body_end + (e - head);
+        const T yv = HY ? y[i] : T(0);
+        o[i] = apply_op_mm<OP, MM, T>(x[i], yv, q, 0);
+    }
+    const char *xb = reinterpret_cast<const char *>(x + head);
+    const char *yb = HY ? reinterpret_cast<const char *>(y + head) : nullptr;
+    char *ob = reinterpret_cast<char *>(o + head);
+    // two vectors per thread in flight per input
+    for (uint64_t v = threadIdx.x; v < nvec; v += 2 * (uint64_t)blockDim.x) {
+        const uint64_t v2 = v + blockDim.x;
+        uint64_t xa[W], ya[W], xc[W], yc[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) ya[k] = yc[k] = 0;
+        ldv<VB, 0>(xb + v * VB, xa);
+        if constexpr (HY) ldv<VB, 0>(yb + v * VB, ya);
+        const bool two = v2 < nvec;
+        if (two) {
+            ldv<VB, 0>(xb + v2 * VB, xc);
+            if constexpr (HY) ldv<VB, 0>(yb + v2 * VB, yc);
+        }
+        uint64_t r[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) r[k] = op_word<OP, T, MM>(xa[k], ya[k], q, k);
+        stv<VB, 0>(ob + v * VB, r);
+        if (two) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) r[k] = op_word<OP, T, MM>(xc[k], yc[k], q, k);
+            stv<VB, 0>(ob + v2 * VB, r);
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void tile_seed(const DevItem &it, uint64_t start, uint64_t cnt) {
+    T *o = static_cast<T *>(it.out) + start;
+    const T lo = (T)it.q;
+    const T span = (T)it.q2 - lo;  // RN(hi - lo) in T, as the host-side generator defines it
+    for (uint64_t e = threadIdx.x; e < cnt; e += blockDim.x)
+        o[e] = seeded_value(splitmix_word(it.seed, it.index_base + start + e), lo, span);
+}
+
+template <int VB>
+__device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint64_t cnt) {
+    const bool f64 = it.dtype == SX_F64;
+    switch (it.op) {
+        case SX_OP_COPY:
+            if (f64) tile_vector<SX_OP_COPY, double, VB, 0>(it, start, cnt);
+            else tile_vector<SX_OP_COPY, float, VB, 0>(it, start, cnt);
+            break;
+        case SX_OP_SCALE:
+            if (f64) tile_vector<SX_OP_SCALE, double, VB, 1>(it, start, cnt);
+            else tile_vector<SX_OP_SCALE, float, VB, 0>(it, start, cnt);
+            break;
+        case SX_OP_ADD:
+            if (f64) tile_vector<SX_OP_ADD, double, VB, 0>(it, start, cnt);
+            else tile_vector<SX_OP_ADD, float, VB, 0>(it, start, cnt);
+            break;
+        case SX_OP_TRIAD:
+            if (f64) tile_vector<SX_OP_TRIAD, double, VB, 1>(it, start, cnt);
+            else tile_vector<SX_OP_TRIAD, float, VB, 0>(it, start, cnt);
+            break;
+        case SX_OP_SEED:
+            if (f64) tile_seed<double>(it, start, cnt);
+            else tile_seed<float>(it, start, cnt);
+            break;
+        default: break;
+    }
+}
+
+template <int VB>
+__global__ void __launch_bounds__(1024)
+k_batch(const DevItem *__restrict__ items, const DevTile *__restrict__ tiles, uint64_t ntiles,
+        uint32_t *done_count, uint64_t *done_ns, uint64_t *t_start) {
+    if (done_count && threadIdx.x == 0) atomicMin((unsigned long long *)t_start, (unsigned long long)global_ns());
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const DevTile tl = tiles[t];
+        const DevItem it = items[tl.item];
+        const uint64_t start = (uint64_t)tl.index * it.tile_elems;
+        const uint64_t cnt = min((uint64_t)it.tile_elems, it.n - start);
+        run_tile<VB>(it, start, cnt);
+        if (done_count) {
+            __syncthreads();  // every thread's stores of this tile are issued
+            if (threadIdx.x == 0) {
+                __threadfence();
+                if (atomicAdd(&done_count[tl.item], 1u) + 1 == it.ntiles)
+                    done_ns[tl.item] = global_ns();
+            }
+        }
+    }
+}
+
+}  // namespace
+}  // namespace sx
 
 using namespace sx;
 
+struct sx_batch {
+    sx_target *t = nullptr;
+    std::vector<sx_batch_item> items;
+    sx_batch_cfg cfg{};
+    uint64_t ntiles = 0, bytes = 0;
+    DevItem *d_items = nullptr;
+    DevTile *d_tiles = nullptr;
+    // completion-recording scratch: counters, stamps, start stamp
+    uint32_t *d_done = nullptr;
+    uint64_t *d_ns = nullptr;
+    bool record = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // per-call baseline completion events
+    std::vector<cudaEvent_t> call_events;
+    cudaEvent_t call_start = nullptr;
+    bool last_was_percall = false;
+};
+
+namespace sx {
+namespace {
+
+double item_bytes(const sx_batch_item &it) {
+    return (double)op_arrays(it.op) * (double)it.n * (double)dtype_size(it.dtype);
+}
+
+int check_items(const sx_batch_item *items, size_t count) {
+    for (size_t i = 0; i < count; ++i) {
+        const auto &it = items[i];
+        if (it.op < SX_OP_COPY || it.op > SX_OP_SEED) return fail(SX_ERR_INVALID, "item %zu: bad op %d", i, it.op);
+        if (it.dtype != SX_F32 && it.dtype != SX_F64) return fail(SX_ERR_DTYPE, "item %zu: dtype %d", i, it.dtype);
+        if (it.n == 0) continue;
+        const bool hy = it.op == SX_OP_ADD || it.op == SX_OP_TRIAD;
+        const bool hx = it.op != SX_OP_SEED;
+        if (!it.out || (hx && !it.x) || (hy && !it.y)) return fail(SX_ERR_INVALID, "item %zu: NULL pointer", i);
+        const size_t es = dtype_size(it.dtype);
+        if ((uintptr_t)it.out % es || (hx && (uintptr_t)it.x % es) || (hy && (uintptr_t)it.y % es))
+            return fail(SX_ERR_INVALID, "item %zu: pointer not aligned to its element type", i);
+        if (it.n > (1ull << 40)) return fail(SX_ERR_INVALID, "item %zu: n too large", i);
+    }
+    return SX_OK;
+}
+
+sx_batch_cfg resolve_batch_cfg(const sx_target *t, const sx_batch_item *items, size_t count,
+                               const sx_batch_cfg *req) {
+    sx_batch_cfg c{};
+    double total = 0;
+    for (size_t i = 0; i < count; ++i) total += item_bytes(items[i]);
+    const double mean = count ? total / count : 0;
+    if (!req || (req->chunk_bytes == 0 && req->threads == 0 && req->blocks_per_sm == 0 && req->vec_bytes == 0)) {
+        if (!tune_batch_lookup(t, mean, &c)) c = sx_batch_cfg{};
+    } else {
+        c = *req;
+    }
+    if (c.chunk_bytes == 0) c.chunk_bytes = 256 * 1024;
+    if (c.threads == 0) c.threads = 512;
+    if (c.blocks_per_sm == 0) c.blocks_per_sm = 4;
+    if (c.vec_bytes == 0) c.vec_bytes = 32;
+    return c;
+}
+
+int validate_batch_cfg(const sx_batch_cfg &c) {
+    if (c.chunk_bytes < 16384 || c.chunk_bytes > (8 << 20))
+        return fail(SX_ERR_INVALID, "chunk_bytes=%d out of [16 KiB, 8 MiB]", c.chunk_bytes);
+    if (c.threads < 64 || c.threads > 1024 || c.threads % 32)
+        return fail(SX_ERR_INVALID, "threads=%d: multiple of 32 in [64, 1024]", c.threads);
+    if (c.blocks_per_sm < 1 || c.blocks_per_sm > 32 || c.blocks_per_sm * c.threads > 2048)
+        return fail(SX_ERR_INVALID, "blocks_per_sm=%d with %d threads exceeds an SM", c.blocks_per_sm, c.threads);
+    if (c.vec_bytes != 16 && c.vec_bytes != 32) return fail(SX_ERR_INVALID, "vec_bytes=%d: 16 or 32", c.vec_bytes);
+    return SX_OK;
+}
+
+void free_device(sx_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_done) cudaFree(b->d_done);
+    if (b->d_ns) cudaFree(b->d_ns);
+    b->d_items = nullptr;
+    b->d_tiles = nullptr;
+    b->d_done = nullptr;
+    b->d_ns = nullptr;
+}
+
+int enqueue_kernel(sx_batch *b, cudaStream_t s) {
+    const size_t count = b->items.size();
+    if (b->record) {
+        SX_CUDA(cudaMemsetAsync(b->d_done, 0, count * sizeof(uint32_t), s));
+        SX_CUDA(cudaMemsetAsync(b->d_ns, 0xFF, sizeof(uint64_t), s));  // t_start = max, then atomicMin
+        SX_CUDA(cudaMemsetAsync(b->d_ns + 1, 0, count * sizeof(uint64_t), s));
+    }
+    if (b->ntiles == 0) return SX_OK;
+    uint64_t grid = (uint64_t)b->t->sm_count * b->cfg.blocks_per_sm;
+    if (grid > b->ntiles) grid = b->ntiles;
+    uint32_t *dc = b->record ? b->d_done : nullptr;
+    uint64_t *dn = b->record ? b->d_ns + 1 : nullptr;
+    uint64_t *ts = b->record ? b->d_ns : nullptr;
+    if (b->cfg.vec_bytes == 16)
+        k_batch<16><<<(unsigned)grid, b->cfg.threads, 0, s>>>(b->d_items, b->d_tiles, b->ntiles, dc, dn, ts);
+    else
+        k_batch<32><<<(unsigned)grid, b->cfg.threads, 0, s>>>(b->d_items, b->d_tiles, b->ntiles, dc, dn, ts);
+    SX_CUDA(cudaGetLastError());
+    return SX_OK;
+}
+
+int capture(sx_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    cudaStream_t cs;
+    SX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int st = SX_OK;
+    if (e == cudaSuccess) {
+        st = enqueue_kernel(b, cs);
+        e = cudaStreamEndCapture(cs, &b->graph);
+    }
+    if (e == cudaSuccess && st == SX_OK) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    cudaStreamDestroy(cs);
+    if (st != SX_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+    return SX_OK;
+}
+
+// (Re)build the device tables and the graph for the batch's items under b->cfg.
+int build(sx_batch *b) {
+    free_device(b);
+    const size_t count = b->items.size();
+    std::vector<DevItem> di(count);
+    std::vector<DevTile> tiles;
+    b->bytes = 0;
+    for (size_t i = 0; i < count; ++i) {
+        const auto &it = b->items[i];
+        DevItem &d = di[i];
+        d.op = (uint32_t)it.op;
+        d.dtype = (uint32_t)it.dtype;
+        d.n = it.n;
+        d.x = it.x;
+        d.y = it.y;
+        d.out = it.out;
+        d.q = it.q;
+        d.q2 = it.q2;
+        d.seed = it.seed;
+        d.index_base = it.index_base;
+        const size_t per_elem = (size_t)op_arrays(it.op) * dtype_size(it.dtype);
+        uint64_t te = (uint64_t)b->cfg.chunk_bytes / per_elem;
+        te = std::max<uint64_t>(64, te / 64 * 64);
+        d.tile_elems = (uint32_t)te;
+        const uint64_t nt = (it.n + te - 1) / te;
+        if (nt > 0xffffffffull) return fail(SX_ERR_INVALID, "item %zu has too many tiles", i);
+        d.ntiles = (uint32_t)nt;
+        for (uint64_t k = 0; k < nt; ++k) tiles.push_back(DevTile{(uint32_t)i, (uint32_t)k});
+        b->bytes += (uint64_t)item_bytes(it);
+    }
+    b->ntiles = tiles.size();
+    SX_CUDA(cudaMalloc(&b->d_items, std::max<size_t>(1, count) * sizeof(DevItem)));
+    SX_CUDA(cudaMalloc(&b->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(DevTile)));
+    SX_CUDA(cudaMalloc(&b->d_done, std::max<size_t>(1, count) * sizeof(uint32_t)));
+    SX_CUDA(cudaMalloc(&b->d_ns, (count + 1) * sizeof(uint64_t)));
+    if (count) SX_CUDA(cudaMemcpy(b->d_items, di.data(), count * sizeof(DevItem), cudaMemcpyHostToDevice));
+    if (!tiles.empty())
+        SX_CUDA(cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(DevTile), cudaMemcpyHostToDevice));
+    return capture(b);
+}
+
+}  // namespace
+}  // namespace sx
+
 extern "C" {
-int sx_batch_create(sx_target *, const sx_batch_item *, size_t, const sx_batch_cfg *, sx_batch **) {
-    return fail(SX_ERR_STATE, "batched launcher not available in this build");
+
+int sx_batch_create(sx_target *t, const sx_batch_item *items, size_t count, const sx_batch_cfg *cfg,
+                    sx_batch **out) {
+    if (!t || !out || (!items && count)) return fail(SX_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    if (count > 0xffffffffull) return fail(SX_ERR_INVALID, "too many items");
+    SX_TRY(check_items(items, count));
+    const sx_batch_cfg c = resolve_batch_cfg(t, items, count, cfg);
+    SX_TRY(validate_batch_cfg(c));
+    DeviceScope ds(t->device);
+    sx_batch *b = new (std::nothrow) sx_batch();
+    if (!b) return fail(SX_ERR_OOM, "host allocation failed");
+    b->t = t;
+    b->items.assign(items, items + count);
+    b->cfg = c;
+    const int st = build(b);
+    if (st != SX_OK) {
+        free_device(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return SX_OK;
 }
-int sx_batch_launch(sx_batch *) { return fail(SX_ERR_STATE, "not available"); }
-int sx_batch_launch_percall(sx_batch *, const sx_launch_cfg *) { return fail(SX_ERR_STATE, "not available"); }
-int sx_batch_set_record(sx_batch *, int) { return fail(SX_ERR_STATE, "not available"); }
-int sx_batch_completion_ns(sx_batch *, uint64_t *, size_t) { return fail(SX_ERR_STATE, "not available"); }
-int sx_batch_info(const sx_batch *, sx_batch_cfg *, uint64_t *, uint64_t *) { return fail(SX_ERR_STATE, "not available"); }
-int sx_batch_destroy(sx_batch *) { return fail(SX_ERR_STATE, "not available"); }
-int sx_tune_batch(sx_batch *, sx_batch_cfg *, float *) { return fail(SX_ERR_STATE, "not available"); }
+
+int sx_batch_launch(sx_batch *b) {
+    if (!b) return fail(SX_ERR_INVALID, "batch is NULL");
+    DeviceScope ds(b->t->device);
+    SX_CUDA(cudaGraphLaunch(b->exec, b->t->stream));
+    b->last_was_percall = false;
+    return SX_OK;
 }
+
+int sx_batch_launch_percall(sx_batch *b, const sx_launch_cfg *cfg) {
+    if (!b) return fail(SX_ERR_INVALID, "batch is NULL");
+    DeviceScope ds(b->t->device);
+    cudaStream_t s = b->t->stream;
+    const size_t count = b->items.size();
+    if (b->record) {
+        if (b->call_events.size() != count) {
+            for (auto ev : b->call_events) cudaEventDestroy(ev);
+            b->call_events.assign(count, nullptr);
+            for (auto &ev : b->call_events) SX_CUDA(cudaEventCreate(&ev));
+        }
+        if (!b->call_start) SX_CUDA(cudaEventCreate(&b->call_start));
+        SX_CUDA(cudaEventRecord(b->call_start, s));
+    }
+    for (size_t i = 0; i < count; ++i) {
+        const auto &it = b->items[i];
+        if (it.op == SX_OP_SEED) {
+            SX_TRY(launch_seed(s, it.dtype, it.out, it.n, it.seed, it.q, it.q2, it.index_base));
+        } else {
+            sx_launch_cfg c = resolve_cfg(b->t, it.op, it.dtype, it.n, cfg);
+            SX_TRY(validate_cfg(b->t, it.op, c));
+            SX_TRY(launch_stream_op(b->t, s, it.op, it.dtype, it.x, it.y, it.out, it.n, it.q, c));
+        }
+        if (b->record) SX_CUDA(cudaEventRecord(b->call_events[i], s));
+    }
+    b->last_was_percall = true;
+    return SX_OK;
+}
+
+int sx_batch_set_record(sx_batch *b, int record) {
+    if (!b) return fail(SX_ERR_INVALID, "batch is NULL");
+    if ((record != 0) == b->record) return SX_OK;
+    DeviceScope ds(b->t->device);
+    SX_CUDA(cudaStreamSynchronize(b->t->stream));
+    b->record = record != 0;
+    return capture(b);
+}
+
+int sx_batch_completion_ns(sx_batch *b, uint64_t *t_ns, size_t count) {
+    if (!b || (!t_ns && count)) return fail(SX_ERR_INVALID, "NULL argument");
+    if (!b->record) return fail(SX_ERR_STATE, "completion recording is off (sx_batch_set_record)");
+    if (count > b->items.size()) return fail(SX_ERR_INVALID, "count exceeds the item count");
+    DeviceScope ds(b->t->device);
+    SX_CUDA(cudaStreamSynchronize(b->t->stream));
+    if (b->last_was_percall) {
+        for (size_t i = 0; i < count; ++i) {
+            float ms = 0;
+            SX_CUDA(cudaEventElapsedTime(&ms, b->call_start, b->call_events[i]));
+            t_ns[i] = (uint64_t)((double)ms * 1e6);
+        }
+        return SX_OK;
+    }
+    std::vector<uint64_t> h(b->items.size() + 1);
+    SX_CUDA(cudaMemcpy(h.data(), b->d_ns, h.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    const uint64_t t0 = h[0];
+    for (size_t i = 0; i < count; ++i) t_ns[i] = (h[i + 1] >= t0 && h[i + 1] != 0) ? h[i + 1] - t0 : 0;
+    return SX_OK;
+}
+
+int sx_batch_info(const sx_batch *b, sx_batch_cfg *cfg, uint64_t *tiles, uint64_t *bytes) {
+    if (!b) return fail(SX_ERR_INVALID, "batch is NULL");
+    if (cfg) *cfg = b->cfg;
+    if (tiles) *tiles = b->ntiles;
+    if (bytes) *bytes = b->bytes;
+    return SX_OK;
+}
+
+int sx_batch_destroy(sx_batch *b) {
+    if (!b) return fail(SX_ERR_INVALID, "batch is NULL");
+    {
+        DeviceScope ds(b->t->device);
+        cudaStreamSynchronize(b->t->stream);
+        free_device(b);
+        for (auto ev : b->call_events) cudaEventDestroy(ev);
+        if (b->call_start) cudaEventDestroy(b->call_start);
+    }
+    delete b;
+    return SX_OK;
+}
+
+int sx_tune_batch(sx_batch *b, sx_batch_cfg *best_out, float *ms_out) {
+    if (!b) return fail(SX_ERR_INVALID, "batch is NULL");
+    DeviceScope ds(b->t->device);
+    cudaStream_t s = b->t->stream;
+    const bool rec = b->record;
+    b->record = false;
+    cudaEvent_t e0, e1;
+    SX_CUDA(cudaEventCreate(&e0));
+    SX_CUDA(cudaEventCreate(&e1));
+    auto time_cfg = [&](const sx_batch_cfg &c, float *ms) -> int {
+        b->cfg = c;
+        SX_TRY(build(b));
+        SX_CUDA(cudaGraphLaunch(b->exec, s));  // warm
+        float best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            cudaEventRecord(e0, s);
+            SX_CUDA(cudaGraphLaunch(b->exec, s));
+            cudaEventRecord(e1, s);
+            SX_CUDA(cudaEventSynchronize(e1));
+            float m = 0;
+            cudaEventElapsedTime(&m, e0, e1);
+            best = std::min(best, m);
+        }
+        *ms = best;
+        return SX_OK;
+    };
+    sx_batch_cfg best = b->cfg;
+    float best_ms = 1e30f;
+    int st = SX_OK;
+    // pass 1: tile size x residency; pass 2: block size and vector width at the best of pass 1
+    for (int chunk : {64 << 10, 128 << 10, 256 << 10, 512 << 10, 1 << 20, 2 << 20})
+        for (int bps : {1, 2, 4, 8}) {
+            sx_batch_cfg c{chunk, 256, bps, 32};
+            float ms = 0;
+            st = time_cfg(c, &ms);
+            if (st != SX_OK) break;
+            if (ms < best_ms) best_ms = ms, best = c;
+        }
+    if (st == SX_OK) {
+        const sx_batch_cfg p1 = best;
+        for (int th : {128, 256, 512, 1024})
+            for (int vb : {16, 32}) {
+                sx_batch_cfg c{p1.chunk_bytes, th, std::max(1, std::min(p1.blocks_per_sm * 256 / th, 2048 / th)), vb};
+                if (validate_batch_cfg(c) != SX_OK) {
+                    clear_error();
+                    continue;
+                }
+                float ms = 0;
+                st = time_cfg(c, &ms);
+                if (st != SX_OK) break;
+                if (ms < best_ms) best_ms = ms, best = c;
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cfg = best;
+    b->record = rec;
+    const int st2 = build(b);
+    if (st != SX_OK) return st;
+    if (st2 != SX_OK) return st2;
+    double total = 0;
+    for (const auto &it : b->items) total += item_bytes(it);
+    tune_batch_store(b->t, b->items.empty() ? 0 : total / b->items.size(), best);
+    if (best_out) *best_out = best;
+    if (ms_out) *ms_out = best_ms;
+    return SX_OK;
+}
+
+}  // extern "C"

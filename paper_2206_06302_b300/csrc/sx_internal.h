@@ -121,7 +121,7 @@ int launch_fill(cudaStream_t stream, int dtype, void *out, size_t n, double valu
 int launch_seed(cudaStream_t stream, int dtype, void *out, size_t n, uint64_t seed, double lo,
                 double hi, uint64_t index_base);
 int launch_stream_fused(const sx_target *t, cudaStream_t stream, int dtype, void *a, void *b,
-                        void *c, size_t n, double q, int iters);
+                        void *c, size_t n, double q, int iters, int fp64_mul);
 int launch_u8_transform(const sx_target *t, cudaStream_t stream, int fn, const void *in,
                         void *out, size_t n);
 // TMA bulk-copy staging family (sx_bulk.cu).

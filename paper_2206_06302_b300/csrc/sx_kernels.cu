@@ -12,6 +12,7 @@
 // issues all loads of a tile before its stores so each thread keeps `unroll` vectors per
 // input in flight, and walks the array with a grid-stride loop or one tile per block.
 // The BULK family (sx_bulk.cu) stages tiles through shared memory with TMA bulk copies.
+#include "sx_device.cuh"
 #include "sx_internal.h"
 
 #include <cstdio>
@@ -20,86 +21,12 @@
 namespace sx {
 namespace {
 
-// ---- element arithmetic ------------------------------------------------------------------
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-
-template <int OP, class T>
-__device__ __forceinline__ T apply_op(T x, T y, T q) {
-    if constexpr (OP == SX_OP_COPY) return x;
-    else if constexpr (OP == SX_OP_SCALE) return mul_rn(x, q);
-    else if constexpr (OP == SX_OP_ADD) return add_rn(x, y);
-    else return add_rn(x, mul_rn(y, q));
-}
-
-// The op on one 64-bit word: one binary64 element or two binary32 elements.
-template <int OP, class T>
-__device__ __forceinline__ uint64_t op_word(uint64_t xw, uint64_t yw, T q) {
-    if constexpr (OP == SX_OP_COPY) {
-        return xw;
-    } else if constexpr (sizeof(T) == 8) {
-        double r = apply_op<OP, double>(__longlong_as_double((long long)xw),
-                                        __longlong_as_double((long long)yw), q);
-        return (uint64_t)__double_as_longlong(r);
-    } else {
-        float r0 = apply_op<OP, float>(__uint_as_float((uint32_t)xw), __uint_as_float((uint32_t)yw), q);
-        float r1 = apply_op<OP, float>(__uint_as_float((uint32_t)(xw >> 32)),
-                                       __uint_as_float((uint32_t)(yw >> 32)), q);
-        return (uint64_t)__float_as_uint(r0) | ((uint64_t)__float_as_uint(r1) << 32);
-    }
-}
-
-// ---- vector loads and stores (inline PTX) ---------------------------------------------------
-// HINT 0: read-only path (ld.global.nc), default stores.
-// HINT 1: streaming: read-only path without L1 allocation and a 256-byte L2 prefetch hint,
-//         evict-first (.cs) stores.
-// HINT 2: coherent loads (ld.global), used when the output aliases an input.
-template <int VB, int HINT>
-__device__ __forceinline__ void ldv(const char *p, uint64_t (&w)[VB / 8]) {
-    if constexpr (VB == 16) {
-        if constexpr (HINT == 0)
-            asm volatile("ld.global.nc.v2.u64 {%0,%1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(p));
-        else if constexpr (HINT == 1)
-            asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v2.u64 {%0,%1}, [%2];"
-                         : "=l"(w[0]), "=l"(w[1]) : "l"(p));
-        else
-            asm volatile("ld.global.v2.u64 {%0,%1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(p));
-    } else {
-        if constexpr (HINT == 0)
-            asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
-                         : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3]) : "l"(p));
-        else if constexpr (HINT == 1)
-            asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u64 {%0,%1,%2,%3}, [%4];"
-                         : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3]) : "l"(p));
-        else
-            asm volatile("ld.global.v4.u64 {%0,%1,%2,%3}, [%4];"
-                         : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3]) : "l"(p));
-    }
-}
-
-template <int VB, int HINT>
-__device__ __forceinline__ void stv(char *p, const uint64_t (&w)[VB / 8]) {
-    if constexpr (VB == 16) {
-        if constexpr (HINT == 1)
-            asm volatile("st.global.cs.v2.u64 [%0], {%1,%2};" ::"l"(p), "l"(w[0]), "l"(w[1]) : "memory");
-        else
-            asm volatile("st.global.v2.u64 [%0], {%1,%2};" ::"l"(p), "l"(w[0]), "l"(w[1]) : "memory");
-    } else {
-        if constexpr (HINT == 1)
-            asm volatile("st.global.cs.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(w[0]), "l"(w[1]),
-                         "l"(w[2]), "l"(w[3]) : "memory");
-        else
-            asm volatile("st.global.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(w[0]), "l"(w[1]),
-                         "l"(w[2]), "l"(w[3]) : "memory");
-    }
-}
+using namespace dev;
 
 // ---- VECTOR kernel -------------------------------------------------------------------------
 // Elements [0, head) and [head + nvec*EPV, n) are done one by one by the first threads of the
 // grid; the body [head, head + nvec*EPV) is nvec vectors of VB bytes, all VB-aligned.
-template <int OP, class T, int VB, int U, int HINT>
+template <int OP, class T, int VB, int U, int HINT, int MM>
 __global__ void __launch_bounds__(1024)
 k_stream_vec(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t nvec, T q) {
     constexpr int W = VB / 8;
@@ -137,7 +64,7 @@ k_stream_vec(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t
             if (v < nvec) {
                 uint64_t r[W];
 #pragma unroll
-                for (int k = 0; k < W; ++k) r[k] = op_word<OP, T>(xw[u][k], yw[u][k], q);
+                for (int k = 0; k < W; ++k) r[k] = op_word<OP, T, MM>(xw[u][k], yw[u][k], q, k);
                 stv<VB, HINT>(ob + v * VB, r);
             }
         }
@@ -155,25 +82,44 @@ __global__ void __launch_bounds__(256) k_stream_scalar(const T *x, const T *y, T
     }
 }
 
-template <int OP, class T, int VB, int U>
-cudaError_t launch_vec_hint(int hint, unsigned blocks, unsigned threads, cudaStream_t s, const T *x,
-                            const T *y, T *out, uint64_t n, uint64_t head, uint64_t nvec, T q) {
-    switch (hint) {
-        case 0: k_stream_vec<OP, T, VB, U, 0><<<blocks, threads, 0, s>>>(x, y, out, n, head, nvec, q); break;
-        case 1: k_stream_vec<OP, T, VB, U, 1><<<blocks, threads, 0, s>>>(x, y, out, n, head, nvec, q); break;
-        default: k_stream_vec<OP, T, VB, U, 2><<<blocks, threads, 0, s>>>(x, y, out, n, head, nvec, q); break;
+struct VecLaunch {
+    unsigned blocks, threads;
+    cudaStream_t s;
+    uint64_t n, head, nvec;
+};
+
+template <int OP, class T, int VB, int U, int HINT>
+void launch_vec_mm(int mm, const VecLaunch &l, const T *x, const T *y, T *out, T q) {
+    // the product unit only matters for binary64 SCALE and TRIAD
+    constexpr bool MUL64 = sizeof(T) == 8 && (OP == SX_OP_SCALE || OP == SX_OP_TRIAD);
+    if constexpr (MUL64) {
+        if (mm == 1) {
+            k_stream_vec<OP, T, VB, U, HINT, 1><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q);
+            return;
+        }
+        if (mm == 2) {
+            k_stream_vec<OP, T, VB, U, HINT, 2><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q);
+            return;
+        }
     }
-    return cudaGetLastError();
+    k_stream_vec<OP, T, VB, U, HINT, 0><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q);
+}
+
+template <int OP, class T, int VB, int U>
+void launch_vec_hint(int hint, int mm, const VecLaunch &l, const T *x, const T *y, T *out, T q) {
+    switch (hint) {
+        case 0: launch_vec_mm<OP, T, VB, U, 0>(mm, l, x, y, out, q); break;
+        case 1: launch_vec_mm<OP, T, VB, U, 1>(mm, l, x, y, out, q); break;
+        default: launch_vec_mm<OP, T, VB, U, 2>(mm, l, x, y, out, q); break;
+    }
 }
 
 template <int OP, class T, int VB>
-cudaError_t launch_vec_unroll(int unroll, int hint, unsigned blocks, unsigned threads, cudaStream_t s,
-                              const T *x, const T *y, T *out, uint64_t n, uint64_t head,
-                              uint64_t nvec, T q) {
+void launch_vec_unroll(int unroll, int hint, int mm, const VecLaunch &l, const T *x, const T *y, T *out, T q) {
     switch (unroll) {
-        case 1: return launch_vec_hint<OP, T, VB, 1>(hint, blocks, threads, s, x, y, out, n, head, nvec, q);
-        case 2: return launch_vec_hint<OP, T, VB, 2>(hint, blocks, threads, s, x, y, out, n, head, nvec, q);
-        default: return launch_vec_hint<OP, T, VB, 4>(hint, blocks, threads, s, x, y, out, n, head, nvec, q);
+        case 1: launch_vec_hint<OP, T, VB, 1>(hint, mm, l, x, y, out, q); break;
+        case 2: launch_vec_hint<OP, T, VB, 2>(hint, mm, l, x, y, out, q); break;
+        default: launch_vec_hint<OP, T, VB, 4>(hint, mm, l, x, y, out, q); break;
     }
 }
 
@@ -219,11 +165,12 @@ int launch_vector(const sx_target *t, cudaStream_t s, const T *x, const T *y, T 
     if (blocks < edge_blocks) blocks = edge_blocks;
     if (blocks == 0) blocks = 1;
     if (blocks > 0x7fffffffull) return fail(SX_ERR_INVALID, "grid too large (%llu blocks)", (unsigned long long)blocks);
-    cudaError_t e;
+    const VecLaunch l{(unsigned)blocks, threads, s, n, head, nvec};
     if (VB == 16)
-        e = launch_vec_unroll<OP, T, 16>(c.unroll, hint, (unsigned)blocks, threads, s, x, y, out, n, head, nvec, q);
+        launch_vec_unroll<OP, T, 16>(c.unroll, hint, c.fp64_mul, l, x, y, out, q);
     else
-        e = launch_vec_unroll<OP, T, 32>(c.unroll, hint, (unsigned)blocks, threads, s, x, y, out, n, head, nvec, q);
+        launch_vec_unroll<OP, T, 32>(c.unroll, hint, c.fp64_mul, l, x, y, out, q);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_stream_vec launch");
     return SX_OK;
 }
@@ -244,29 +191,18 @@ int dispatch_op(const sx_target *t, cudaStream_t s, int op, const void *x, const
     }
 }
 
-// ---- seeded bulk construction (SplitMix64, counter form) ------------------------------------
-__device__ __forceinline__ uint64_t splitmix_word(uint64_t seed, uint64_t i) {
-    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
+// ---- seeded bulk construction ---------------------------------------------------------------
 __global__ void k_seed_f64(double *out, uint64_t n, uint64_t seed, double lo, double span, uint64_t base) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t w = splitmix_word(seed, base + i);
-        const double u = __dmul_rn(__ull2double_rn(w >> 11), 0x1p-53);
-        out[i] = __dadd_rn(lo, __dmul_rn(span, u));
+        out[i] = seeded_value(splitmix_word(seed, base + i), lo, span);
     }
 }
 
 __global__ void k_seed_f32(float *out, uint64_t n, uint64_t seed, float lo, float span, uint64_t base) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t w = splitmix_word(seed, base + i);
-        const float u = __fmul_rn(__uint2float_rn((uint32_t)(w >> 40)), 0x1p-24f);
-        out[i] = __fadd_rn(lo, __fmul_rn(span, u));
+        out[i] = seeded_value(splitmix_word(seed, base + i), lo, span);
     }
 }
 
@@ -288,22 +224,22 @@ unsigned setup_blocks(size_t n) {
 // Scale b=RN(c*q), Add c=RN(a+b), Triad a=RN(b+RN(c*q)).  One kernel can run the whole chain
 // per element from one read of a and write a, b, c once, bit-identical to four launches per
 // pass.
-template <class T>
-__device__ __forceinline__ void fused_chain(T &a, T &b, T &c, T q, int iters) {
+template <int MM, class T>
+__device__ __forceinline__ void fused_chain(T &a, T &b, T &c, T q, int iters, int lane) {
     for (int k = 0; k < iters; ++k) {
         c = a;
-        b = mul_rn(c, q);
+        b = mul_sel<MM>(c, q, lane);
         c = add_rn(a, b);
-        a = add_rn(b, mul_rn(c, q));
+        a = add_rn(b, mul_sel<MM>(c, q, lane + 1));
     }
 }
 
-template <class T>
+template <class T, int MM>
 __global__ void __launch_bounds__(256) k_stream_fused(T *a, T *b, T *c, uint64_t n, T q, int iters) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         T av = a[i], bv, cv;
-        fused_chain(av, bv, cv, q, iters);
+        fused_chain<MM>(av, bv, cv, q, iters, 0);
         a[i] = av;
         b[i] = bv;
         c[i] = cv;
@@ -311,7 +247,7 @@ __global__ void __launch_bounds__(256) k_stream_fused(T *a, T *b, T *c, uint64_t
 }
 
 // 16-byte vector form of the fused kernel for arrays that are all 16-byte aligned.
-template <class T>
+template <class T, int MM>
 __global__ void __launch_bounds__(256) k_stream_fused_v(T *a, T *b, T *c, uint64_t nvec, T q, int iters) {
     constexpr int EPV = 16 / sizeof(T);
     using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
@@ -321,7 +257,7 @@ __global__ void __launch_bounds__(256) k_stream_fused_v(T *a, T *b, T *c, uint64
         T ae[EPV], be[EPV], ce[EPV];
         memcpy(ae, &av, 16);
 #pragma unroll
-        for (int k = 0; k < EPV; ++k) fused_chain(ae[k], be[k], ce[k], q, iters);
+        for (int k = 0; k < EPV; ++k) fused_chain<MM>(ae[k], be[k], ce[k], q, iters, k);
         V ao, bo, co;
         memcpy(&ao, ae, 16);
         memcpy(&bo, be, 16);
@@ -410,6 +346,8 @@ int validate_cfg(const sx_target *t, int op, const sx_launch_cfg &c) {
             return fail(SX_ERR_INVALID, "blocks_per_sm=%d out of [0, 64]", c.blocks_per_sm);
         if (c.cache_hint < 0 || c.cache_hint > 1)
             return fail(SX_ERR_INVALID, "cache_hint=%d: need 0 or 1", c.cache_hint);
+        if (c.fp64_mul < 0 || c.fp64_mul > 2)
+            return fail(SX_ERR_INVALID, "fp64_mul=%d: need 0, 1 or 2", c.fp64_mul);
         return SX_OK;
     }
     if (c.variant == SX_VARIANT_BULK) return validate_bulk_cfg(t, op, c);
@@ -455,7 +393,7 @@ int launch_seed(cudaStream_t s, int dtype, void *out, size_t n, uint64_t seed, d
 }
 
 int launch_stream_fused(const sx_target *t, cudaStream_t s, int dtype, void *a, void *b, void *c,
-                        size_t n, double q, int iters) {
+                        size_t n, double q, int iters, int mm) {
     if (n == 0 || iters <= 0) return SX_OK;
     const size_t es = dtype_size(dtype);
     const bool aligned = ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0) &&
@@ -465,17 +403,23 @@ int launch_stream_fused(const sx_target *t, cudaStream_t s, int dtype, void *a, 
         const uint64_t nvec = n * es / 16;
         uint64_t blocks = (nvec + 255) / 256;
         if (blocks > cap) blocks = cap;
-        if (dtype == SX_F64)
-            k_stream_fused_v<double><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, nvec, q, iters);
+        if (dtype == SX_F64 && mm == 1)
+            k_stream_fused_v<double, 1><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, nvec, q, iters);
+        else if (dtype == SX_F64 && mm == 2)
+            k_stream_fused_v<double, 2><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, nvec, q, iters);
+        else if (dtype == SX_F64)
+            k_stream_fused_v<double, 0><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, nvec, q, iters);
         else
-            k_stream_fused_v<float><<<(unsigned)blocks, 256, 0, s>>>((float *)a, (float *)b, (float *)c, nvec, (float)q, iters);
+            k_stream_fused_v<float, 0><<<(unsigned)blocks, 256, 0, s>>>((float *)a, (float *)b, (float *)c, nvec, (float)q, iters);
     } else {
         uint64_t blocks = (n + 255) / 256;
         if (blocks > cap) blocks = cap;
-        if (dtype == SX_F64)
-            k_stream_fused<double><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, n, q, iters);
+        if (dtype == SX_F64 && mm != 0)
+            k_stream_fused<double, 1><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, n, q, iters);
+        else if (dtype == SX_F64)
+            k_stream_fused<double, 0><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, n, q, iters);
         else
-            k_stream_fused<float><<<(unsigned)blocks, 256, 0, s>>>((float *)a, (float *)b, (float *)c, n, (float)q, iters);
+            k_stream_fused<float, 0><<<(unsigned)blocks, 256, 0, s>>>((float *)a, (float *)b, (float *)c, n, (float)q, iters);
     }
     SX_CUDA(cudaGetLastError());
     return SX_OK;

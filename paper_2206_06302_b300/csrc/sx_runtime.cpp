@@ -559,7 +559,10 @@ int sx_stream_iter(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double
 int sx_stream_fused(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double q, int iters) {
     SX_TRY(check_stream_arrays(e, a, b, c, iters));
     DeviceScope ds(e->t->device);
-    SX_TRY(launch_stream_fused(e->t, e->t->stream, a->dtype, a->ptr, b->ptr, c->ptr, a->n, q, iters));
+    // the chain is four binary64 operations per pass, two of them products: by default the
+    // products go to the integer units (bit-identical), unless the executor fixes fp64_mul
+    const int mm = e->fixed_cfg ? e->cfg.fp64_mul : 1;
+    SX_TRY(launch_stream_fused(e->t, e->t->stream, a->dtype, a->ptr, b->ptr, c->ptr, a->n, q, iters, mm));
     return finish_call(e);
 }
 

@@ -172,20 +172,25 @@ void tune_batch_store(const sx_target *t, double mean_item_bytes, const sx_batch
 // Candidate shapes: a first pass over the per-thread access pattern (vector width, unroll,
 // cache hint) at a fixed block shape, then a pass over the block shape (threads, blocks per
 // SM or one tile per block) for the best access pattern, then the BULK family.
-static std::vector<sx_launch_cfg> vector_pass1() {
+static bool mul64(int op, int dtype) { return dtype == SX_F64 && (op == SX_OP_SCALE || op == SX_OP_TRIAD); }
+
+static std::vector<sx_launch_cfg> vector_pass1(int op, int dtype) {
     std::vector<sx_launch_cfg> v;
+    const int nmm = mul64(op, dtype) ? 3 : 1;
     for (int vb : {16, 32})
         for (int u : {1, 2, 4})
-            for (int h : {0, 1}) {
-                sx_launch_cfg c{};
-                c.variant = SX_VARIANT_VECTOR;
-                c.threads = 256;
-                c.blocks_per_sm = 0;
-                c.vec_bytes = vb;
-                c.unroll = u;
-                c.cache_hint = h;
-                v.push_back(c);
-            }
+            for (int h : {0, 1})
+                for (int mm = 0; mm < nmm; ++mm) {
+                    sx_launch_cfg c{};
+                    c.variant = SX_VARIANT_VECTOR;
+                    c.threads = 256;
+                    c.blocks_per_sm = 0;
+                    c.vec_bytes = vb;
+                    c.unroll = u;
+                    c.cache_hint = h;
+                    c.fp64_mul = mm;
+                    v.push_back(c);
+                }
     return v;
 }
 
@@ -202,8 +207,9 @@ static std::vector<sx_launch_cfg> vector_pass2(const sx_launch_cfg &best) {
     return v;
 }
 
-static std::vector<sx_launch_cfg> bulk_candidates() {
+static std::vector<sx_launch_cfg> bulk_candidates(int op, int dtype) {
     std::vector<sx_launch_cfg> v;
+    const int mm = mul64(op, dtype) ? 1 : 0;
     for (int tile : {8192, 16384, 32768})
         for (int st : {2, 3, 4, 6})
             for (int th : {128, 256}) {
@@ -213,6 +219,7 @@ static std::vector<sx_launch_cfg> bulk_candidates() {
                 c.blocks_per_sm = 1;
                 c.tile_bytes = tile;
                 c.stages = st;
+                c.fp64_mul = mm;
                 v.push_back(c);
             }
     return v;
@@ -259,13 +266,11 @@ int sx_tune(sx_target *t, sx_op op, sx_dtype dtype, size_t n, sx_launch_cfg *bes
         }
     };
     if (st == SX_OK) {
-        for (const auto &c : vector_pass1()) try_cfg(c);
+        for (const auto &c : vector_pass1(op, dtype)) try_cfg(c);
         const sx_launch_cfg b1 = best;
         for (const auto &c : vector_pass2(b1)) try_cfg(c);
-        if (validate_bulk_cfg(t, op, bulk_candidates()[0]) == SX_OK)
-            for (const auto &c : bulk_candidates()) try_cfg(c);
-        else
-            clear_error();
+        for (const auto &c : bulk_candidates(op, dtype)) try_cfg(c);
+        clear_error();
         if (best.variant == 0) st = fail(SX_ERR_CUDA, "no candidate launch shape ran");
         else st = check_device_error(t);
     }
@@ -310,7 +315,7 @@ int sx_tune_save(const char *path) {
                << ", \"threads\": " << c.threads << ", \"blocks_per_sm\": " << c.blocks_per_sm
                << ", \"vec_bytes\": " << c.vec_bytes << ", \"unroll\": " << c.unroll
                << ", \"cache_hint\": " << c.cache_hint << ", \"tile_bytes\": " << c.tile_bytes
-               << ", \"stages\": " << c.stages << "}";
+               << ", \"stages\": " << c.stages << ", \"fp64_mul\": " << c.fp64_mul << "}";
             first = false;
         }
         os << "\n  ],\n  \"batch\": [";
@@ -359,6 +364,7 @@ int sx_tune_load(const char *path) {
                     c.cache_hint = geti(kv, "cache_hint");
                     c.tile_bytes = geti(kv, "tile_bytes");
                     c.stages = geti(kv, "stages");
+                    c.fp64_mul = geti(kv, "fp64_mul");
                     ops[OpKey{kv["device"], geti(kv, "op"), geti(kv, "dtype"), geti(kv, "bucket")}] = c;
                 } else if (section == "batch") {
                     sx_batch_cfg c{};

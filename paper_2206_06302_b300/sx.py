@@ -43,7 +43,8 @@ class SxError(RuntimeError):
 # ---- structures --------------------------------------------------------------------------------
 class sx_launch_cfg(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("variant", "threads", "blocks_per_sm", "vec_bytes",
-                                         "unroll", "cache_hint", "tile_bytes", "stages")]
+                                         "unroll", "cache_hint", "tile_bytes", "stages",
+                                         "fp64_mul", "reserved")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

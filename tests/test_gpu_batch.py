@@ -1,0 +1,168 @@
+"""GPU parity of the persistent batched launcher (bulk_execute over many instances) and of its
+one-launch-per-instance baseline: every instance's output must equal the oracle's bit for bit,
+whatever the tile size, block shape or vector width, with ragged and misaligned instances."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2206_06302_b300 as sx
+import stream_inputs as si
+from gpu_util import assert_bitwise
+
+pytestmark = pytest.mark.gpu
+
+OPN = {sx.SX_OP_COPY: "copy", sx.SX_OP_SCALE: "scale", sx.SX_OP_ADD: "add", sx.SX_OP_TRIAD: "triad"}
+
+
+class Workload:
+    """`count` instances carved from one device buffer; some start off the vector alignment."""
+
+    def __init__(self, count, seed, lo_exp=0, hi_exp=16, with_seed_items=True):
+        import torch
+        ops = [sx.SX_OP_COPY, sx.SX_OP_SCALE, sx.SX_OP_ADD, sx.SX_OP_TRIAD]
+        if with_seed_items:
+            ops.append(sx.SX_OP_SEED)
+        lens = si.log_uniform_lengths(si.word_scalar(seed, 1), count, lo_exp, hi_exp)
+        opi = si.words(si.word_scalar(seed, 2), count) % np.uint64(len(ops))
+        dti = si.words(si.word_scalar(seed, 3), count) % np.uint64(2)
+        offs = si.words(si.word_scalar(seed, 4), count) % np.uint64(4)
+        self.specs = []
+        total = 0
+        for k in range(count):
+            op = ops[int(opi[k])]
+            dt = np.float64 if dti[k] else np.float32
+            es = np.dtype(dt).itemsize
+            n = int(lens[k])
+            off = int(offs[k]) * es if k % 3 == 0 else 0  # every third instance misaligned
+            mixed = k % 5 == 1  # and every fifth has arrays misaligned differently
+            regions = []
+            for j in range(3):
+                total = (total + 255) // 256 * 256 + (j * es if mixed else off)
+                regions.append(total)
+                total += n * es
+            self.specs.append(dict(op=op, dt=dt, n=n, regions=regions, q=[3.0, -0.7, 1.5][k % 3],
+                                   seed=int(si.word_scalar(seed, 1000 + k)), base=k * 17))
+        self.buf = torch.zeros(total + 256, dtype=torch.uint8, device="cuda")
+        self.base = self.buf.data_ptr()
+        self.host_in = []
+        import torch as _t
+        for k, s in enumerate(self.specs):
+            x = si.uniform(si.array_seed(seed, 0, k), s["n"], s["dt"])
+            y = si.uniform(si.array_seed(seed, 1, k), s["n"], s["dt"])
+            self.host_in.append((x, y))
+            for arr, r in ((x, s["regions"][0]), (y, s["regions"][1])):
+                nb = arr.nbytes
+                self.buf[r:r + nb] = _t.from_numpy(arr.view(np.uint8)).cuda()
+        _t.cuda.synchronize()
+
+    def items(self):
+        out = []
+        for s in self.specs:
+            r = s["regions"]
+            out.append(sx.sx_batch_item(
+                op=s["op"], dtype=sx.SX_F64 if s["dt"] == np.float64 else sx.SX_F32, n=s["n"],
+                x=self.base + r[0], y=self.base + r[1], out=self.base + r[2],
+                q=s["q"] if s["op"] != sx.SX_OP_SEED else -1.0, q2=1.0 if s["op"] == sx.SX_OP_SEED else 0.0,
+                seed=s["seed"], index_base=s["base"]))
+        return out
+
+    def clear_outputs(self):
+        for s in self.specs:
+            r = s["regions"][2]
+            self.buf[r:r + s["n"] * np.dtype(s["dt"]).itemsize] = 0xEE
+
+    def check(self, what):
+        import torch
+        torch.cuda.synchronize()
+        h = self.buf.cpu().numpy()
+        for k, s in enumerate(self.specs):
+            dt, n = s["dt"], s["n"]
+            r = s["regions"][2]
+            got = h[r:r + n * np.dtype(dt).itemsize].view(dt)
+            x, y = self.host_in[k]
+            if s["op"] == sx.SX_OP_SEED:
+                want = si.uniform(s["seed"], n, dt, -1.0, 1.0, start=s["base"])
+            else:
+                want = oracle.apply(OPN[s["op"]], x, y, s["q"])
+            assert_bitwise(got, want, f"{what}: instance {k} ({s['op']}, {dt.__name__}, n={n})")
+
+
+CFGS = [None,
+        dict(chunk_bytes=16384, threads=128, blocks_per_sm=1, vec_bytes=16),
+        dict(chunk_bytes=65536, threads=256, blocks_per_sm=8, vec_bytes=32),
+        dict(chunk_bytes=1 << 20, threads=1024, blocks_per_sm=2, vec_bytes=32)]
+
+
+@pytest.mark.parametrize("cfg", range(len(CFGS)))
+def test_batch_matches_oracle(target, cfg):
+    w = Workload(300, seed=11)
+    b = sx.sx_batch_create(target, w.items(), CFGS[cfg])
+    for rep in range(2):  # the captured graph replays
+        w.clear_outputs()
+        sx.sx_batch_launch(b)
+        sx.sx_target_synchronize(target)
+        w.check(f"graph launch {rep}")
+    sx.sx_batch_destroy(b)
+
+
+def test_percall_baseline_matches_oracle(target):
+    w = Workload(120, seed=12)
+    b = sx.sx_batch_create(target, w.items())
+    w.clear_outputs()
+    sx.sx_batch_launch_percall(b)
+    sx.sx_target_synchronize(target)
+    w.check("per-call")
+    sx.sx_batch_destroy(b)
+
+
+def test_completion_recording(target):
+    w = Workload(64, seed=13, lo_exp=10, hi_exp=20)
+    b = sx.sx_batch_create(target, w.items())
+    sx.sx_batch_set_record(b, True)
+    for launch in (sx.sx_batch_launch, sx.sx_batch_launch_percall):
+        w.clear_outputs()
+        launch(b)
+        t = sx.sx_batch_completion_ns(b, 64)
+        w.check(launch.__name__)
+        assert all(v > 0 for v in t) and max(t) < 5e9
+    sx.sx_batch_destroy(b)
+
+
+def test_empty_and_zero_length_items(target):
+    b = sx.sx_batch_create(target, [])
+    sx.sx_batch_launch(b)
+    sx.sx_target_synchronize(target)
+    sx.sx_batch_destroy(b)
+    w = Workload(10, seed=14)
+    items = w.items()
+    items[3].n = 0
+    w.specs[3]["n"] = 0
+    b = sx.sx_batch_create(target, items)
+    sx.sx_batch_launch(b)
+    w.check("with an empty item")
+    sx.sx_batch_destroy(b)
+
+
+def test_batch_autotune_keeps_results(target):
+    w = Workload(200, seed=15, lo_exp=8, hi_exp=18, with_seed_items=False)
+    b = sx.sx_batch_create(target, w.items())
+    best, ms = sx.sx_tune_batch(b)
+    assert ms > 0 and best["chunk_bytes"] >= 16384
+    w.clear_outputs()
+    sx.sx_batch_launch(b)
+    w.check("after tuning")
+    cfg, tiles, nbytes = sx.sx_batch_info(b)
+    assert cfg == best and tiles > 0 and nbytes > 0
+    sx.sx_batch_destroy(b)
+
+
+def test_bad_items_are_rejected(target):
+    it = sx.sx_batch_item(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=10, x=None, y=None, out=None)
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_batch_create(target, [it])
+    assert ei.value.status == sx.SX_ERR_INVALID
+    it = sx.sx_batch_item(op=9, dtype=sx.SX_F64, n=10)
+    with pytest.raises(sx.SxError):
+        sx.sx_batch_create(target, [it])
+    with pytest.raises(sx.SxError):
+        sx.sx_batch_create(target, [], dict(chunk_bytes=100, threads=256, blocks_per_sm=1, vec_bytes=32))

@@ -21,13 +21,22 @@ OPS = {"copy": sx.SX_OP_COPY, "scale": sx.SX_OP_SCALE, "add": sx.SX_OP_ADD,
        "triad": sx.SX_OP_TRIAD}
 SIZES = [1, 2, 3, 5, 7, 8, 31, 33, 255, 257, 1000, 4099, 65537, (1 << 20) + 3]
 
-VECTOR_CFGS = [
+CFGS = [
     None,  # executor default / tuner table
     dict(variant=sx.SX_VARIANT_VECTOR, threads=256, vec_bytes=16, unroll=1),
-    dict(variant=sx.SX_VARIANT_VECTOR, threads=128, vec_bytes=32, unroll=4, blocks_per_sm=2),
-    dict(variant=sx.SX_VARIANT_VECTOR, threads=1024, vec_bytes=32, unroll=2, cache_hint=1),
+    dict(variant=sx.SX_VARIANT_VECTOR, threads=128, vec_bytes=32, unroll=4, blocks_per_sm=2,
+         fp64_mul=1),
+    dict(variant=sx.SX_VARIANT_VECTOR, threads=1024, vec_bytes=32, unroll=2, cache_hint=1,
+         fp64_mul=2),
     dict(variant=sx.SX_VARIANT_VECTOR, threads=512, vec_bytes=16, unroll=4, blocks_per_sm=1,
-         cache_hint=1),
+         cache_hint=1, fp64_mul=1),
+    # TMA bulk-copy staging: tiles of 1 KiB make even the mid sizes span many tiles and blocks
+    dict(variant=sx.SX_VARIANT_BULK, threads=128, blocks_per_sm=1, tile_bytes=1024, stages=2),
+    dict(variant=sx.SX_VARIANT_BULK, threads=256, blocks_per_sm=2, tile_bytes=4096, stages=4,
+         fp64_mul=1),
+    dict(variant=sx.SX_VARIANT_BULK, threads=512, blocks_per_sm=1, tile_bytes=16384, stages=6,
+         fp64_mul=2),
+    dict(variant=sx.SX_VARIANT_BULK, threads=256, blocks_per_sm=1, tile_bytes=32768, stages=3),
 ]
 
 
@@ -53,14 +62,14 @@ def _run_op(target, cfg, op, x, y, q, dt):
     return got
 
 
-@pytest.mark.parametrize("cfg", range(len(VECTOR_CFGS)))
+@pytest.mark.parametrize("cfg", range(len(CFGS)))
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 @pytest.mark.parametrize("op", list(OPS))
-def test_vector_parity_sizes(target, op, dt, cfg):
+def test_parity_sizes(target, op, dt, cfg):
     for n in SIZES:
         x, y = _inputs(n, dt)
         for q in (3.0, -0.1):
-            got = _run_op(target, VECTOR_CFGS[cfg], op, x, y, q, dt)
+            got = _run_op(target, CFGS[cfg], op, x, y, q, dt)
             assert_bitwise(got, oracle.apply(op, x, y, q), f"{op} {dt.__name__} n={n} q={q}")
 
 
@@ -299,3 +308,73 @@ def test_stream_host_end_to_end(target, executor):
         assert_bitwise(hc, c)
         for h in (da, db, dc):
             sx.sx_free(h)
+
+
+def _random_doubles(n, seed):
+    """Bit patterns spread over every binary64 exponent (zeros, subnormals, normals near the
+    overflow threshold, infinities and NaNs included)."""
+    w = si.words(seed, n)
+    return w.view(np.float64).copy()
+
+
+@pytest.mark.parametrize("variant", [sx.SX_VARIANT_VECTOR, sx.SX_VARIANT_BULK])
+def test_integer_unit_product_is_bit_identical(target, executor, variant):
+    """fp64_mul=1/2 (integer-unit RN-even product with FP64-pipe fallback) == fp64_mul=0 bit for
+    bit on every bit pattern, and == the oracle wherever the result is not a generated NaN."""
+    n = (1 << 20) + 5
+    x = _random_doubles(n, 31)
+    y = _random_doubles(n, 32)
+    base = dict(variant=variant, threads=256)
+    if variant == sx.SX_VARIANT_BULK:
+        base.update(tile_bytes=8192, stages=3, blocks_per_sm=1)
+    else:
+        base.update(vec_bytes=32, unroll=2)
+    qs = [3.0, -0.1, 1.0, 2.0 ** -1022, 5e-324, 1.7976931348623157e308, 1e-300, 1e300,
+          float.fromhex("0x1.fffffffffffffp-1"), -7.5, float("inf"), 0.0]
+    for op in ("scale", "triad"):
+        for q in qs:
+            outs = [_run_op(target, dict(base, fp64_mul=mm), op, x, y, q, np.float64)
+                    for mm in (0, 1, 2)]
+            assert_bitwise(outs[1], outs[0], f"{op} q={q} mm=1")
+            assert_bitwise(outs[2], outs[0], f"{op} q={q} mm=2")
+            want = oracle.apply(op, x, y, q)
+            ok = ~np.isnan(want)
+            assert_bitwise(outs[1][ok], want[ok], f"{op} q={q} vs oracle")
+            assert np.array_equal(np.isnan(outs[1]), np.isnan(want))
+
+
+def test_integer_unit_product_near_thresholds(target, executor):
+    """Products that round up into the next binade, to DBL_MAX / overflow, and across the
+    normal/subnormal boundary."""
+    vals = []
+    for e in (-1022, -1021, -1000, -520, -1, 0, 1, 511, 1000, 1022, 1023):
+        for m in ("0x1.0000000000000", "0x1.0000000000001", "0x1.fffffffffffff", "0x1.5555555555555",
+                  "0x1.aaaaaaaaaaaab", "0x1.8000000000000", "0x1.7ffffffffffff"):
+            v = float.fromhex(f"{m}p{e}")
+            vals += [v, -v]
+    x = np.array(vals, np.float64)
+    y = x[::-1].copy()
+    qs = [3.0, float.fromhex("0x1.5555555555555p-2"), float.fromhex("0x1.fffffffffffffp+0"),
+          float.fromhex("0x1.0000000000001p+0"), 0.5, 2.0 ** -52, 2.0 ** 52, 2.0 ** -1022 * 3,
+          float.fromhex("0x1.8p-1023")]
+    for q in qs:
+        for op in ("scale", "triad"):
+            want = oracle.apply(op, x, y, q)
+            for mm in (1, 2):
+                got = _run_op(target, dict(variant=sx.SX_VARIANT_VECTOR, threads=128, vec_bytes=16,
+                                           unroll=1, fp64_mul=mm), op, x, y, q, np.float64)
+                ok = ~np.isnan(want)
+                assert_bitwise(got[ok], want[ok], f"{op} q={q!r} mm={mm}")
+
+
+@pytest.mark.parametrize("mm", [0, 1, 2])
+def test_fused_product_units(target, mm):
+    e = sx.sx_executor_create(target, sx.SX_PAR, dict(variant=sx.SX_VARIANT_VECTOR, fp64_mul=mm))
+    n = 40001
+    a, b, c = si.stream_arrays(n, np.float64, base_seed=8)
+    ga, gb, gc = _stream_device(target, e, a, b, c, 3.0, 7, fused=True)
+    oracle.stream(a, b, c, 3.0, 7)
+    assert_bitwise(ga, a)
+    assert_bitwise(gb, b)
+    assert_bitwise(gc, c)
+    sx.sx_executor_destroy(e)
