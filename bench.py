@@ -204,6 +204,151 @@ def stream_kernels(sx, torch, t, stream, e, dtype_code, n, steps, warmup, seed_i
     return arrs, seq, one_pass, events, es
 
 
+def _pct(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(p / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def batched_section(sx, torch, t, stream, args, rank):
+    """4096 independent FP64 triad/add instances, lengths log-uniform in [2^10, 2^22]: one
+    persistent graph-captured launch (autotuned shape) vs one launch per instance."""
+    import oracle
+    import stream_inputs as si
+    inst = si.batched_instances(si.BASE_SEED + rank, args.batch_count)
+    offs, total = [], 0
+    for _, n in inst:
+        r = []
+        for _ in range(3):
+            total = (total + 255) // 256 * 256
+            r.append(total)
+            total += n * 8
+        offs.append(r)
+    buf = sx.sx_alloc(t, sx.SX_U8, total)
+    base = sx.sx_array_data(buf)[0]
+    seeds = []
+    for k, (_, n) in enumerate(inst):
+        for j in (0, 1):
+            seeds.append(sx.sx_batch_item(op=sx.SX_OP_SEED, dtype=sx.SX_F64, n=n, out=base + offs[k][j],
+                                          q=-1.0, q2=1.0, seed=si.array_seed(si.BASE_SEED, j, k)))
+    sb = sx.sx_batch_create(t, seeds)
+    sx.sx_batch_launch(sb)
+    sx.sx_target_synchronize(t)
+    sx.sx_batch_destroy(sb)
+    code = {"add": sx.SX_OP_ADD, "triad": sx.SX_OP_TRIAD}
+    items = [sx.sx_batch_item(op=code[op], dtype=sx.SX_F64, n=n, x=base + o[0], y=base + o[1],
+                              out=base + o[2], q=Q) for (op, n), o in zip(inst, offs)]
+    b = sx.sx_batch_create(t, items)
+    best, _ = sx.sx_tune_batch(b)
+    cfg, tiles, nbytes = sx.sx_batch_info(b)
+
+    def timed(launch, reps):
+        for _ in range(2):
+            launch()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        for r in range(reps):
+            ev[2 * r].record(stream)
+            launch()
+            ev[2 * r + 1].record(stream)
+        torch.cuda.synchronize()
+        return sorted(ev[2 * r].elapsed_time(ev[2 * r + 1]) for r in range(reps))
+
+    g_ms = timed(lambda: sx.sx_batch_launch(b), args.batch_reps)
+    p_ms = timed(lambda: sx.sx_batch_launch_percall(b), max(3, args.batch_reps // 2))
+    sx.sx_batch_set_record(b, True)
+    sx.sx_batch_launch(b)
+    comp_g = [v / 1e6 for v in sx.sx_batch_completion_ns(b, len(items))]
+    sx.sx_batch_launch_percall(b)
+    comp_p = [v / 1e6 for v in sx.sx_batch_completion_ns(b, len(items))]
+    sx.sx_batch_set_record(b, False)
+    sx.sx_batch_launch(b)
+    sx.sx_target_synchronize(t)
+    # spot check: 8 instances, whole arrays, against the oracle
+    ok = True
+    for k in range(0, len(items), max(1, len(items) // 8)):
+        op, n = inst[k]
+        got = []
+        for j in range(3):
+            h = np.empty(n, np.float64)
+            w = sx.sx_array_wrap(t, sx.SX_F64, base + offs[k][j], n)
+            sx.sx_copy_d2h(h.ctypes.data, w, n)
+            sx.sx_free(w)
+            got.append(h)
+        x = si.uniform(si.array_seed(si.BASE_SEED, 0, k), n, np.float64)
+        y = si.uniform(si.array_seed(si.BASE_SEED, 1, k), n, np.float64)
+        want = oracle.apply(op, x, y, Q)
+        ok &= bool(np.array_equal(got[0].view(np.uint64), x.view(np.uint64)) and
+                   np.array_equal(got[2].view(np.uint64), want.view(np.uint64)))
+    sx.sx_batch_destroy(b)
+    sx.sx_free(buf)
+    gm, pm = g_ms[len(g_ms) // 2], p_ms[len(p_ms) // 2]
+    return {
+        "workload": f"{len(items)} FP64 triad/add instances, n log-uniform in [2^10, 2^22] "
+                    f"(seeded), {nbytes / 1e9:.1f} GB moved per launch",
+        "tuned": cfg, "tiles": tiles,
+        "graph_ms": round(gm, 4), "graph_GB/s": round(nbytes / (gm * 1e-3) / 1e9, 1),
+        "percall_ms": round(pm, 4), "percall_GB/s": round(nbytes / (pm * 1e-3) / 1e9, 1),
+        "speedup": round(pm / gm, 3),
+        "completion_ms_p50": {"graph": round(_pct(comp_g, 50), 4), "percall": round(_pct(comp_p, 50), 4)},
+        "completion_ms_p99": {"graph": round(_pct(comp_g, 99), 4), "percall": round(_pct(comp_p, 99), 4)},
+        "launches": {"graph": 1, "percall": len(items)},
+        "spot_check_vs_oracle": ok,
+    }
+
+
+def served_section(sx, torch, t, stream, args, rank):
+    """Poisson stream of copy/scale/add/triad requests (FP64/FP32), n log-uniform in
+    [2^12, 2^28], inputs constructed on the device, 64 GB arena: continuous batching vs the
+    per-call FIFO at several offered loads."""
+    import stream_inputs as si
+    reqs = si.poisson_requests(si.BASE_SEED + 7 + rank, args.serve_count, rate_per_s=1.0)
+    ops = {"copy": sx.SX_OP_COPY, "scale": sx.SX_OP_SCALE, "add": sx.SX_OP_ADD, "triad": sx.SX_OP_TRIAD}
+    dts = {"f64": (sx.SX_F64, 8), "f32": (sx.SX_F32, 4)}
+    work = []
+    bytes_total = 0
+    for k, r in enumerate(reqs):
+        code, es = dts[r["dtype"]]
+        two = r["op"] in ("add", "triad")
+        bytes_total += r["n"] * es * ((2 if two else 1) + (3 if two else 2))
+        work.append(sx.sx_request(op=ops[r["op"]], dtype=code, n=r["n"], q=Q,
+                                  seed_x=si.word_scalar(r["seed"], 0), seed_y=si.word_scalar(r["seed"], 1),
+                                  lo=-1.0, hi=1.0, flags=sx.SX_REQ_AUTO_RELEASE))
+    mean_bytes = bytes_total / len(reqs)
+    capacity_bw = 6.5e12  # nominal service rate used only to set the offered load
+    out = {"workload": f"{len(reqs)} Poisson requests, ops uniform over copy/scale/add/triad, "
+                       f"FP64/FP32 50/50, n log-uniform in [2^12, 2^28], inputs constructed on "
+                       f"device, {args.serve_budget_gb:g} GB arena, mean {mean_bytes / 1e6:.1f} MB "
+                       f"moved per request", "runs": []}
+    for load in [float(v) for v in args.serve_loads.split(",") if v]:
+        rate = load * capacity_bw / mean_bytes
+        times = [r["t"] / rate for r in reqs]
+        for mode, name in ((sx.SX_SERVE_CONTINUOUS, "continuous"), (sx.SX_SERVE_FIFO, "fifo")):
+            s = sx.sx_server_create(t, budget_bytes=int(args.serve_budget_gb * 1e9), mode=mode)
+            ids = sx.sx_server_replay(s, work, times)
+            lat, t0, t1, rej = [], None, None, 0
+            for rid in ids:
+                st = sx.sx_server_wait(s, rid, 600000)
+                if st["state"] == sx.SX_REQ_REJECTED:
+                    rej += 1
+                    continue
+                lat.append((st["t_done"] - st["t_submit"]) * 1e3)
+                t0 = st["t_submit"] if t0 is None else min(t0, st["t_submit"])
+                t1 = st["t_done"] if t1 is None else max(t1, st["t_done"])
+            stats = sx.sx_server_stats_get(s)
+            sx.sx_server_destroy(s)
+            out["runs"].append({
+                "mode": name, "offered_load": load, "rate_per_s": round(rate, 1),
+                "p50_ms": round(_pct(lat, 50), 4), "p99_ms": round(_pct(lat, 99), 4),
+                "mean_ms": round(sum(lat) / len(lat), 4),
+                "GB/s": round(stats["bytes_moved"] / (t1 - t0) / 1e9, 1),
+                "launches": stats["launches"], "steps": stats["steps"], "rejected": rej,
+                "arena_peak_GB": round(stats["arena_peak"] / 1e9, 2)})
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_2206_06302_b300 as sx
@@ -326,11 +471,9 @@ def run_ours(args):
     # ---- sections beyond the plain pass --------------------------------------------------------
     extra = {}
     if not args.quick and "batched" in args.sections:
-        from bench_sections import batched_section
-        extra["batched"] = batched_section(sx, torch, t, stream, args)
+        extra["batched"] = batched_section(sx, torch, t, stream, args, rank)
     if not args.quick and "served" in args.sections:
-        from bench_sections import served_section
-        extra["served"] = served_section(sx, torch, t, stream, args)
+        extra["served"] = served_section(sx, torch, t, stream, args, rank)
 
     # ---- CPU oracle on a bounded sample (rank 0, N=1 only) ------------------------------------
     cpu = None
@@ -389,7 +532,12 @@ def main(argv=None):
     ap.add_argument("--cpu-n", type=int, default=1 << 24)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--sections", default="")
+    ap.add_argument("--sections", default="batched,served")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-reps", type=int, default=10)
+    ap.add_argument("--serve-count", type=int, default=2000)
+    ap.add_argument("--serve-loads", default="0.5,0.8,0.95")
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -305,21 +305,31 @@ int sx_tune_clear(void);
 /* ---- serving loop: continuous batching of STREAM requests on device-resident arrays ---- */
 typedef struct sx_server sx_server;
 
+/* Modes.  CONTINUOUS: the server thread runs "steps"; each step is one launch of the batched
+ * kernel holding a piece of every active request's current phase (inputs construction, then the
+ * operation), the step's byte budget shared out so that short requests finish in one step and
+ * long ones share the rest.  Requests that arrive while steps are on the GPU are admitted as
+ * slots and arena memory free up and join the next step.  FIFO: the per-call baseline; each
+ * admitted request is enqueued at once as its own launches (construct x, construct y, op) on
+ * the stream, in arrival order. */
 enum { SX_SERVE_CONTINUOUS = 0, SX_SERVE_FIFO = 1 };
 typedef struct sx_server_cfg {
-    uint64_t budget_bytes;   /* device arena the server allocates once; admission bound    */
-    int32_t mode;            /* SX_SERVE_CONTINUOUS: each step runs a chunk of every active
-                                request in one launch; SX_SERVE_FIFO: one request at a time,
-                                one launch per phase, in arrival order (the per-call baseline) */
-    int32_t max_active;      /* requests admitted at once (slots), 1..4096                 */
-    int32_t chunk_bytes;     /* CONTINUOUS: bytes a request may move per step               */
-    int32_t steps_in_flight; /* CONTINUOUS: launched steps not yet completed (1..8)         */
-    int32_t threads, blocks_per_sm, vec_bytes, reserved;
+    uint64_t budget_bytes;   /* device arena the server allocates once; admission bound      */
+    int32_t mode;            /* SX_SERVE_CONTINUOUS or SX_SERVE_FIFO                          */
+    int32_t max_active;      /* requests admitted at once (slots), 1..65536; 0 = 256          */
+    int32_t chunk_bytes;     /* CONTINUOUS: byte budget of one step (1 MiB..2 GiB); 0 = 256 MiB */
+    int32_t steps_in_flight; /* CONTINUOUS: launched steps not yet completed (1..8); 0 = 3    */
+    int32_t threads, blocks_per_sm, vec_bytes;  /* batched-kernel shape; 0 = default        */
+    int32_t tile_bytes;      /* CONTINUOUS: work-tile bytes of the batched kernel; 0 = 256 KiB */
 } sx_server_cfg;
 
+/* Request flags. */
+enum { SX_REQ_AUTO_RELEASE = 1 /* free the arrays as soon as the request is DONE */ };
+
 /* One request: construct its inputs on the device from seeds (x from seed_x, y from seed_y,
- * uniform in [lo, hi)), then run `op` into `out`.  x, y and out live in the server's arena
- * from admission until sx_server_release. */
+ * uniform in [lo, hi), see sx_seed_uniform), then run `op` into `out`.  x, y and out live in
+ * the server's arena from admission until sx_server_release (or completion, with
+ * SX_REQ_AUTO_RELEASE). */
 typedef struct sx_request {
     int32_t op;      /* COPY..TRIAD */
     int32_t dtype;   /* SX_F32 / SX_F64 */
@@ -327,6 +337,8 @@ typedef struct sx_request {
     double q;
     uint64_t seed_x, seed_y;
     double lo, hi;
+    uint32_t flags;  /* SX_REQ_* flags */
+    uint32_t reserved;
 } sx_request;
 
 enum { SX_REQ_QUEUED = 0, SX_REQ_ACTIVE = 1, SX_REQ_DONE = 2, SX_REQ_REJECTED = 3,
@@ -354,6 +366,10 @@ int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out);
 /* Queue a request; *id identifies it.  Requests larger than the arena are rejected at once
  * (state REJECTED, status SX_ERR_OOM); others wait until slots and arena memory free up. */
 int sx_server_submit(sx_server *s, const sx_request *r, uint64_t *id);
+/* Open-loop load: a library thread submits reqs[k] at t_arrival[k] seconds (non-decreasing)
+ * after this call; ids[k] receives each request's id at once.  Returns immediately. */
+int sx_server_replay(sx_server *s, const sx_request *reqs, const double *t_arrival, size_t count,
+                     uint64_t *ids);
 int sx_server_poll(sx_server *s, uint64_t id, sx_request_status *st);
 /* Wait until the request is DONE or REJECTED (SX_ERR_TIMEOUT after timeout_ms >= 0). */
 int sx_server_wait(sx_server *s, uint64_t id, int64_t timeout_ms, sx_request_status *st);

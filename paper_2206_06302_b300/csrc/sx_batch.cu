@@ -34,7 +34,15 @@ struct DevItem {
     double q, q2;
     uint64_t seed, index_base;
     uint32_t tile_elems, ntiles;
+    uint32_t mulv;  // product variant of FP64 SCALE/TRIAD (0, 2 or 4; see mul_sel)
+    uint32_t pad;
 };
+
+// Batches split each FP64 product between the integer units and the FP64 pipe.
+inline uint32_t item_mul_variant(const sx_batch_item &it) {
+    const bool mul64 = it.dtype == SX_F64 && (it.op == SX_OP_SCALE || it.op == SX_OP_TRIAD);
+    return mul64 ? (uint32_t)mul_variant(2, it.q) : 0u;
+}
 
 struct DevTile {
     uint32_t item;
@@ -112,16 +120,20 @@ __device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint
             else tile_vector<SX_OP_COPY, float, VB, 0>(it, start, cnt);
             break;
         case SX_OP_SCALE:
-            if (f64) tile_vector<SX_OP_SCALE, double, VB, 1>(it, start, cnt);
-            else tile_vector<SX_OP_SCALE, float, VB, 0>(it, start, cnt);
+            if (!f64) tile_vector<SX_OP_SCALE, float, VB, 0>(it, start, cnt);
+            else if (it.mulv == 4) tile_vector<SX_OP_SCALE, double, VB, 4>(it, start, cnt);
+            else if (it.mulv == 2) tile_vector<SX_OP_SCALE, double, VB, 2>(it, start, cnt);
+            else tile_vector<SX_OP_SCALE, double, VB, 0>(it, start, cnt);
             break;
         case SX_OP_ADD:
             if (f64) tile_vector<SX_OP_ADD, double, VB, 0>(it, start, cnt);
             else tile_vector<SX_OP_ADD, float, VB, 0>(it, start, cnt);
             break;
         case SX_OP_TRIAD:
-            if (f64) tile_vector<SX_OP_TRIAD, double, VB, 1>(it, start, cnt);
-            else tile_vector<SX_OP_TRIAD, float, VB, 0>(it, start, cnt);
+            if (!f64) tile_vector<SX_OP_TRIAD, float, VB, 0>(it, start, cnt);
+            else if (it.mulv == 4) tile_vector<SX_OP_TRIAD, double, VB, 4>(it, start, cnt);
+            else if (it.mulv == 2) tile_vector<SX_OP_TRIAD, double, VB, 2>(it, start, cnt);
+            else tile_vector<SX_OP_TRIAD, double, VB, 0>(it, start, cnt);
             break;
         case SX_OP_SEED:
             if (f64) tile_seed<double>(it, start, cnt);
@@ -286,15 +298,21 @@ int capture(sx_batch *b) {
     return SX_OK;
 }
 
-// (Re)build the device tables and the graph for the batch's items under b->cfg.
-int build(sx_batch *b) {
-    free_device(b);
-    const size_t count = b->items.size();
-    std::vector<DevItem> di(count);
-    std::vector<DevTile> tiles;
-    b->bytes = 0;
+// Elements per work tile of an item for tiles of about `tile_bytes` moved bytes: a multiple of
+// 64 elements, so vector alignment carries from one tile to the next.
+uint64_t tile_elems_for(const sx_batch_item &it, int tile_bytes) {
+    const size_t per_elem = (size_t)op_arrays(it.op) * dtype_size(it.dtype);
+    const uint64_t te = (uint64_t)tile_bytes / per_elem;
+    return std::max<uint64_t>(64, te / 64 * 64);
+}
+
+// Fill the device-layout item table and append the item-major tile list.
+int fill_tables(const sx_batch_item *items, size_t count, int tile_bytes, DevItem *di, DevTile *tiles,
+                size_t tile_cap, size_t *ntiles, uint64_t *bytes) {
+    size_t nt_total = 0;
+    uint64_t by = 0;
     for (size_t i = 0; i < count; ++i) {
-        const auto &it = b->items[i];
+        const auto &it = items[i];
         DevItem &d = di[i];
         d.op = (uint32_t)it.op;
         d.dtype = (uint32_t)it.dtype;
@@ -306,17 +324,42 @@ int build(sx_batch *b) {
         d.q2 = it.q2;
         d.seed = it.seed;
         d.index_base = it.index_base;
-        const size_t per_elem = (size_t)op_arrays(it.op) * dtype_size(it.dtype);
-        uint64_t te = (uint64_t)b->cfg.chunk_bytes / per_elem;
-        te = std::max<uint64_t>(64, te / 64 * 64);
+        d.mulv = item_mul_variant(it);
+        d.pad = 0;
+        const uint64_t te = tile_elems_for(it, tile_bytes);
         d.tile_elems = (uint32_t)te;
         const uint64_t nt = (it.n + te - 1) / te;
         if (nt > 0xffffffffull) return fail(SX_ERR_INVALID, "item %zu has too many tiles", i);
         d.ntiles = (uint32_t)nt;
-        for (uint64_t k = 0; k < nt; ++k) tiles.push_back(DevTile{(uint32_t)i, (uint32_t)k});
-        b->bytes += (uint64_t)item_bytes(it);
+        if (nt_total + nt > tile_cap) return fail(SX_ERR_INVALID, "tile table overflow");
+        for (uint64_t k = 0; k < nt; ++k) tiles[nt_total + k] = DevTile{(uint32_t)i, (uint32_t)k};
+        nt_total += nt;
+        by += (uint64_t)item_bytes(it);
     }
-    b->ntiles = tiles.size();
+    *ntiles = nt_total;
+    if (bytes) *bytes = by;
+    return SX_OK;
+}
+
+size_t count_tiles(const sx_batch_item *items, size_t count, int tile_bytes) {
+    size_t nt = 0;
+    for (size_t i = 0; i < count; ++i) {
+        const uint64_t te = tile_elems_for(items[i], tile_bytes);
+        nt += (items[i].n + te - 1) / te;
+    }
+    return nt;
+}
+
+// (Re)build the device tables and the graph for the batch's items under b->cfg.
+int build(sx_batch *b) {
+    free_device(b);
+    const size_t count = b->items.size();
+    std::vector<DevItem> di(count);
+    std::vector<DevTile> tiles(count_tiles(b->items.data(), count, b->cfg.chunk_bytes));
+    size_t nt = 0;
+    SX_TRY(fill_tables(b->items.data(), count, b->cfg.chunk_bytes, di.data(), tiles.data(), tiles.size(),
+                       &nt, &b->bytes));
+    b->ntiles = nt;
     SX_CUDA(cudaMalloc(&b->d_items, std::max<size_t>(1, count) * sizeof(DevItem)));
     SX_CUDA(cudaMalloc(&b->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(DevTile)));
     SX_CUDA(cudaMalloc(&b->d_done, std::max<size_t>(1, count) * sizeof(uint32_t)));
@@ -328,6 +371,70 @@ int build(sx_batch *b) {
 }
 
 }  // namespace
+
+// ---- item lists built per launch (the serving loop's steps) ------------------------------------
+size_t step_tile_count(const sx_batch_item *items, size_t count, int tile_bytes) {
+    return count_tiles(items, count, tile_bytes);
+}
+
+void step_slot_free(StepSlot &s) {
+    if (s.h_items) cudaFreeHost(s.h_items);
+    if (s.h_tiles) cudaFreeHost(s.h_tiles);
+    if (s.d_items) cudaFree(s.d_items);
+    if (s.d_tiles) cudaFree(s.d_tiles);
+    if (s.done) cudaEventDestroy(s.done);
+    s = StepSlot{};
+}
+
+int step_slot_reserve(StepSlot &s, size_t items, size_t tiles) {
+    if (!s.done) SX_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+    if (items > s.cap_items) {
+        const size_t cap = std::max<size_t>(items, 2 * s.cap_items);
+        if (s.h_items) cudaFreeHost(s.h_items);
+        if (s.d_items) cudaFree(s.d_items);
+        s.h_items = s.d_items = nullptr;
+        s.cap_items = 0;
+        SX_CUDA(cudaMallocHost(&s.h_items, cap * sizeof(DevItem)));
+        SX_CUDA(cudaMalloc(&s.d_items, cap * sizeof(DevItem)));
+        s.cap_items = cap;
+    }
+    if (tiles > s.cap_tiles) {
+        const size_t cap = std::max<size_t>(tiles, 2 * s.cap_tiles);
+        if (s.h_tiles) cudaFreeHost(s.h_tiles);
+        if (s.d_tiles) cudaFree(s.d_tiles);
+        s.h_tiles = s.d_tiles = nullptr;
+        s.cap_tiles = 0;
+        SX_CUDA(cudaMallocHost(&s.h_tiles, cap * sizeof(DevTile)));
+        SX_CUDA(cudaMalloc(&s.d_tiles, cap * sizeof(DevTile)));
+        s.cap_tiles = cap;
+    }
+    return SX_OK;
+}
+
+int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const sx_batch_item *items, size_t count,
+                const sx_batch_cfg &cfg) {
+    const size_t want = count_tiles(items, count, cfg.chunk_bytes);
+    SX_TRY(step_slot_reserve(s, std::max<size_t>(1, count), std::max<size_t>(1, want)));
+    size_t nt = 0;
+    SX_TRY(fill_tables(items, count, cfg.chunk_bytes, static_cast<DevItem *>(s.h_items),
+                       static_cast<DevTile *>(s.h_tiles), s.cap_tiles, &nt, nullptr));
+    if (nt > 0) {
+        SX_CUDA(cudaMemcpyAsync(s.d_items, s.h_items, count * sizeof(DevItem), cudaMemcpyHostToDevice, stream));
+        SX_CUDA(cudaMemcpyAsync(s.d_tiles, s.h_tiles, nt * sizeof(DevTile), cudaMemcpyHostToDevice, stream));
+        uint64_t grid = (uint64_t)t->sm_count * cfg.blocks_per_sm;
+        if (grid > nt) grid = nt;
+        const DevItem *di = static_cast<const DevItem *>(s.d_items);
+        const DevTile *dt = static_cast<const DevTile *>(s.d_tiles);
+        if (cfg.vec_bytes == 16)
+            k_batch<16><<<(unsigned)grid, cfg.threads, 0, stream>>>(di, dt, nt, nullptr, nullptr, nullptr);
+        else
+            k_batch<32><<<(unsigned)grid, cfg.threads, 0, stream>>>(di, dt, nt, nullptr, nullptr, nullptr);
+        SX_CUDA(cudaGetLastError());
+    }
+    SX_CUDA(cudaEventRecord(s.done, stream));
+    return SX_OK;
+}
+
 }  // namespace sx
 
 extern "C" {

@@ -224,10 +224,16 @@ int launch_bulk_t(const sx_target *t, cudaStream_t st, const T *x, const T *y, T
     constexpr bool MUL64 = sizeof(T) == 8 && (OP == SX_OP_SCALE || OP == SX_OP_TRIAD);
     auto kern = k_stream_bulk<OP, T, 0>;
     if constexpr (MUL64) {
-        if (c.fp64_mul == 1) kern = k_stream_bulk<OP, T, 1>;
-        else if (c.fp64_mul == 2) kern = k_stream_bulk<OP, T, 2>;
+        switch (mul_variant(c.fp64_mul, (double)q)) {
+            case 1: kern = k_stream_bulk<OP, T, 1>; break;
+            case 2: kern = k_stream_bulk<OP, T, 2>; break;
+            case 3: kern = k_stream_bulk<OP, T, 3>; break;
+            case 4: kern = k_stream_bulk<OP, T, 4>; break;
+            default: break;
+        }
     }
-    // raise the dynamic shared memory limit of this instantiation on first use (per device)
+    // raise this instantiation's dynamic shared memory limit (cheap; repeated per launch so
+    // that every device the kernel runs on has it)
     SX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     SX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, c.threads, smem));

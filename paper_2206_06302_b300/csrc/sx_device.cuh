@@ -29,35 +29,68 @@ __host__ __device__ constexpr bool has_y() { return OP == SX_OP_ADD || OP == SX_
 // Whenever c or q is zero, subnormal, infinite or NaN, or the rounded result would be
 // subnormal or overflow, it defers to the FP64 pipe (__dmul_rn), so the result is bit-identical
 // to __dmul_rn for every input.
+//
+// The fallback sits in a function that is never inlined: an inlined DMUL would be if-converted
+// into a predicated instruction that still occupies the FP64 pipe for every element.
+static __device__ __noinline__ double dmul_fallback(double c, double q) { return __dmul_rn(c, q); }
+
+//
+// SHORT selects, at compile time, the path for a scalar whose significand has at most 11
+// significant bits (q = 3.0 has two): the caller guarantees it (see q_short_significand).
+template <bool SHORT>
 __device__ __forceinline__ double mul_rn_int(double c, double q) {
     const uint64_t cb = (uint64_t)__double_as_longlong(c);
     const uint64_t qb = (uint64_t)__double_as_longlong(q);
     const uint32_t ce = (uint32_t)(cb >> 52) & 0x7FFu;
     const uint32_t qe = (uint32_t)(qb >> 52) & 0x7FFu;
-    const uint64_t a = (cb << 11) | 0x8000000000000000ull;  // significand, leading bit at 63
-    const uint64_t b = (qb << 11) | 0x8000000000000000ull;
-    const uint64_t hi = __umul64hi(a, b);  // product / 2^64, in [2^62, 2^64)
-    const uint64_t lo = a * b;
-    const uint32_t top = (uint32_t)(hi >> 63);  // product significand in [2, 4)
-    const uint32_t sh = 10u + top;
-    uint64_t m = hi >> sh;                       // 53 bits
-    const uint64_t rb = (hi >> (sh - 1)) & 1u;   // first dropped bit
-    const uint64_t st = (hi & ((1ull << (sh - 1)) - 1)) | lo;
-    m += rb & ((st != 0) | (m & 1u));            // ties to even
-    const int e = (int)ce + (int)qe - 1023 + (int)top;  // biased exponent before the carry
+    // q-only quantities (loop invariant): q = Qs * 2^tz * 2^(qe-1075) with Qs odd
+    const uint64_t qsig = (qb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const uint32_t tz = (uint32_t)__ffsll((long long)qsig) - 1u;
+    const uint64_t qs = qsig >> tz;
+    const uint32_t L = 64u - (uint32_t)__clzll((long long)qs);  // bits of Qs, 1..53
+    const uint64_t mc = (cb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    uint64_t m;
+    int e;
+    if constexpr (SHORT) {
+        // short significand (q = 3 has two bits): Mc*Qs < 2^64 is exact in one word
+        const uint64_t p = mc * qs;                         // in [2^(51+L), 2^(53+L))
+        const uint32_t top = (uint32_t)(p >> (52u + L)) & 1u;
+        const uint32_t s = L - 1u + top;                    // bits dropped to keep 53
+        m = p >> s;
+        const uint64_t rb = s ? (p >> (s - 1u)) & 1u : 0u;
+        const uint64_t st = s > 1u ? p & ((1ull << (s - 1u)) - 1u) : 0u;
+        m += rb & ((st != 0) | (m & 1u));                   // ties to even
+        e = (int)ce + (int)qe + (int)s + (int)tz - 1075;
+    } else {
+        const uint64_t a = mc << 11;                        // leading bit at 63
+        const uint64_t b = qsig << 11;
+        const uint64_t hi = __umul64hi(a, b);               // product / 2^64, in [2^62, 2^64)
+        const uint64_t lo = a * b;
+        const uint32_t top = (uint32_t)(hi >> 63);          // product significand in [2, 4)
+        const uint32_t sh = 10u + top;
+        m = hi >> sh;                                       // 53 bits
+        const uint64_t rb = (hi >> (sh - 1)) & 1u;          // first dropped bit
+        const uint64_t st = (hi & ((1ull << (sh - 1)) - 1)) | lo;
+        m += rb & ((st != 0) | (m & 1u));                   // ties to even
+        e = (int)ce + (int)qe - 1023 + (int)top;            // biased exponent before the carry
+    }
     const int ef = e + (int)(m >> 53);
     const bool ok = (ce - 1u < 2046u) & (qe - 1u < 2046u) & (e >= 1) & (ef <= 2046);
-    if (!ok) return __dmul_rn(c, q);
+    if (!ok) return dmul_fallback(c, q);
     const uint64_t bits = ((uint64_t)e << 52) + (m - (1ull << 52));  // a carry bumps the exponent
     return __longlong_as_double((long long)(bits | ((cb ^ qb) & 0x8000000000000000ull)));
 }
 
-// Product used by SCALE/TRIAD: MM 0 = FP64 pipe, 1 = integer units, 2 = alternate the two by
-// the parity of `k` (the word index within a thread's vector).
+// Product used by SCALE/TRIAD, by kernel variant MM:
+//   0 = FP64 pipe; 1 = integer units; 2 = integer units and FP64 pipe alternating by the parity
+//   of `k` (the word index within a thread's vector); 3 and 4 = as 1 and 2 with the
+//   short-significand path.  The host picks MM from the launch's fp64_mul and q (mul_variant).
 template <int MM, class T>
 __device__ __forceinline__ T mul_sel(T x, T q, int k) {
-    if constexpr (sizeof(T) == 8 && MM == 1) return mul_rn_int(x, q);
-    else if constexpr (sizeof(T) == 8 && MM == 2) return (k & 1) ? mul_rn(x, q) : mul_rn_int(x, q);
+    if constexpr (sizeof(T) == 8 && MM == 1) return mul_rn_int<false>(x, q);
+    else if constexpr (sizeof(T) == 8 && MM == 2) return (k & 1) ? mul_rn(x, q) : mul_rn_int<false>(x, q);
+    else if constexpr (sizeof(T) == 8 && MM == 3) return mul_rn_int<true>(x, q);
+    else if constexpr (sizeof(T) == 8 && MM == 4) return (k & 1) ? mul_rn(x, q) : mul_rn_int<true>(x, q);
     else return mul_rn(x, q);
 }
 

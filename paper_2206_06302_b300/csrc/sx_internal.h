@@ -44,6 +44,27 @@ struct DeviceScope {
     }
 };
 
+// True if the binary64 q is normal and its significand has at most 11 significant bits.
+inline bool q_short_significand(double q) {
+    uint64_t b;
+    std::memcpy(&b, &q, sizeof b);
+    const uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
+    if (e == 0 || e == 0x7FF) return false;
+    uint64_t s = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    s >>= __builtin_ctzll(s);
+    return s < (1ull << 11);
+}
+
+// Kernel product variant (see mul_sel) for a launch's fp64_mul on q.  The integer path only
+// pays off for normal q; for zero, subnormal, infinite or NaN q every element would fall back.
+inline int mul_variant(int fp64_mul, double q) {
+    uint64_t b;
+    std::memcpy(&b, &q, sizeof b);
+    const uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
+    if (fp64_mul == 0 || e == 0 || e == 0x7FF) return 0;
+    return q_short_significand(q) ? fp64_mul + 2 : fp64_mul;
+}
+
 inline size_t dtype_size(int dt) {
     switch (dt) {
         case SX_F32: return 4;
@@ -134,6 +155,23 @@ sx_launch_cfg resolve_cfg(const sx_target *t, int op, int dtype, size_t n, const
 int validate_cfg(const sx_target *t, int op, const sx_launch_cfg &cfg);
 // Reads and clears the target's device error word.
 int check_device_error(const sx_target *t);
+
+// ---- batched kernel over item lists built per launch (sx_batch.cu) ----------------------------
+// Staging of one launch: pinned host tables, device tables, and an event recorded after the
+// kernel.  A slot may be refilled once its event has completed.
+struct StepSlot {
+    void *h_items = nullptr, *h_tiles = nullptr, *d_items = nullptr, *d_tiles = nullptr;
+    size_t cap_items = 0, cap_tiles = 0;
+    cudaEvent_t done = nullptr;
+};
+int step_slot_reserve(StepSlot &s, size_t items, size_t tiles);
+void step_slot_free(StepSlot &s);
+// Number of work tiles `items` are cut into with tiles of `tile_bytes`.
+size_t step_tile_count(const sx_batch_item *items, size_t count, int tile_bytes);
+// Cut `items` into tiles of cfg.chunk_bytes, stage the tables, launch the batched kernel on
+// `stream` and record s.done after it.
+int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const sx_batch_item *items,
+                size_t count, const sx_batch_cfg &cfg);
 
 // ---- autotuner table (sx_tune.cpp) ------------------------------------------------------
 bool tune_table_lookup(const sx_target *t, int op, int dtype, size_t n, sx_launch_cfg *cfg);

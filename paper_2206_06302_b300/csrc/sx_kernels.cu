@@ -91,15 +91,15 @@ struct VecLaunch {
 template <int OP, class T, int VB, int U, int HINT>
 void launch_vec_mm(int mm, const VecLaunch &l, const T *x, const T *y, T *out, T q) {
     // the product unit only matters for binary64 SCALE and TRIAD
-    constexpr bool MUL64 = sizeof(T) == 8 && (OP == SX_OP_SCALE || OP == SX_OP_TRIAD);
+    // (aliased outputs, HINT 2, keep the FP64 pipe: a rare case not worth more instantiations)
+    constexpr bool MUL64 = sizeof(T) == 8 && (OP == SX_OP_SCALE || OP == SX_OP_TRIAD) && HINT != 2;
     if constexpr (MUL64) {
-        if (mm == 1) {
-            k_stream_vec<OP, T, VB, U, HINT, 1><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q);
-            return;
-        }
-        if (mm == 2) {
-            k_stream_vec<OP, T, VB, U, HINT, 2><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q);
-            return;
+        switch (mm) {
+            case 1: k_stream_vec<OP, T, VB, U, HINT, 1><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q); return;
+            case 2: k_stream_vec<OP, T, VB, U, HINT, 2><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q); return;
+            case 3: k_stream_vec<OP, T, VB, U, HINT, 3><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q); return;
+            case 4: k_stream_vec<OP, T, VB, U, HINT, 4><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q); return;
+            default: break;
         }
     }
     k_stream_vec<OP, T, VB, U, HINT, 0><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q);
@@ -166,10 +166,11 @@ int launch_vector(const sx_target *t, cudaStream_t s, const T *x, const T *y, T 
     if (blocks == 0) blocks = 1;
     if (blocks > 0x7fffffffull) return fail(SX_ERR_INVALID, "grid too large (%llu blocks)", (unsigned long long)blocks);
     const VecLaunch l{(unsigned)blocks, threads, s, n, head, nvec};
+    const int mm = mul_variant(c.fp64_mul, (double)q);
     if (VB == 16)
-        launch_vec_unroll<OP, T, 16>(c.unroll, hint, c.fp64_mul, l, x, y, out, q);
+        launch_vec_unroll<OP, T, 16>(c.unroll, hint, mm, l, x, y, out, q);
     else
-        launch_vec_unroll<OP, T, 32>(c.unroll, hint, c.fp64_mul, l, x, y, out, q);
+        launch_vec_unroll<OP, T, 32>(c.unroll, hint, mm, l, x, y, out, q);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_stream_vec launch");
     return SX_OK;
@@ -399,27 +400,29 @@ int launch_stream_fused(const sx_target *t, cudaStream_t s, int dtype, void *a, 
     const bool aligned = ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0) &&
                          ((uintptr_t)c % 16 == 0) && ((n * es) % 16 == 0);
     const uint64_t cap = (uint64_t)t->sm_count * 8;
+    const int v = dtype == SX_F64 ? mul_variant(mm, q) : 0;
+    double *a8 = (double *)a, *b8 = (double *)b, *c8 = (double *)c;
     if (aligned) {
         const uint64_t nvec = n * es / 16;
         uint64_t blocks = (nvec + 255) / 256;
         if (blocks > cap) blocks = cap;
-        if (dtype == SX_F64 && mm == 1)
-            k_stream_fused_v<double, 1><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, nvec, q, iters);
-        else if (dtype == SX_F64 && mm == 2)
-            k_stream_fused_v<double, 2><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, nvec, q, iters);
-        else if (dtype == SX_F64)
-            k_stream_fused_v<double, 0><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, nvec, q, iters);
-        else
-            k_stream_fused_v<float, 0><<<(unsigned)blocks, 256, 0, s>>>((float *)a, (float *)b, (float *)c, nvec, (float)q, iters);
+        const unsigned g = (unsigned)blocks;
+        if (dtype == SX_F32)
+            k_stream_fused_v<float, 0><<<g, 256, 0, s>>>((float *)a, (float *)b, (float *)c, nvec, (float)q, iters);
+        else if (v == 1) k_stream_fused_v<double, 1><<<g, 256, 0, s>>>(a8, b8, c8, nvec, q, iters);
+        else if (v == 2) k_stream_fused_v<double, 2><<<g, 256, 0, s>>>(a8, b8, c8, nvec, q, iters);
+        else if (v == 3) k_stream_fused_v<double, 3><<<g, 256, 0, s>>>(a8, b8, c8, nvec, q, iters);
+        else if (v == 4) k_stream_fused_v<double, 4><<<g, 256, 0, s>>>(a8, b8, c8, nvec, q, iters);
+        else k_stream_fused_v<double, 0><<<g, 256, 0, s>>>(a8, b8, c8, nvec, q, iters);
     } else {
         uint64_t blocks = (n + 255) / 256;
         if (blocks > cap) blocks = cap;
-        if (dtype == SX_F64 && mm != 0)
-            k_stream_fused<double, 1><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, n, q, iters);
-        else if (dtype == SX_F64)
-            k_stream_fused<double, 0><<<(unsigned)blocks, 256, 0, s>>>((double *)a, (double *)b, (double *)c, n, q, iters);
-        else
-            k_stream_fused<float, 0><<<(unsigned)blocks, 256, 0, s>>>((float *)a, (float *)b, (float *)c, n, (float)q, iters);
+        const unsigned g = (unsigned)blocks;
+        if (dtype == SX_F32)
+            k_stream_fused<float, 0><<<g, 256, 0, s>>>((float *)a, (float *)b, (float *)c, n, (float)q, iters);
+        else if (v == 1 || v == 2) k_stream_fused<double, 1><<<g, 256, 0, s>>>(a8, b8, c8, n, q, iters);
+        else if (v == 3 || v == 4) k_stream_fused<double, 3><<<g, 256, 0, s>>>(a8, b8, c8, n, q, iters);
+        else k_stream_fused<double, 0><<<g, 256, 0, s>>>(a8, b8, c8, n, q, iters);
     }
     SX_CUDA(cudaGetLastError());
     return SX_OK;

@@ -1,15 +1,701 @@
-// sx_server.cpp -- placeholder until the serving loop is built.
+// sx_server.cpp -- a serving loop for STREAM requests on device-resident arrays.
+//
+// A request asks for `op` over n elements whose inputs are constructed on the device from
+// seeds (Section 3.2's bulk construction, offloaded to the GPU as in Section 4.2) and whose
+// output stays resident until the client releases it.  The server thread owns one device arena
+// of budget_bytes; a request is admitted when a slot is free and its arrays fit in the arena
+// (first fit, address-ordered free list with coalescing), otherwise it waits.  Requests larger
+// than the whole arena are rejected at submission.
+//
+// CONTINUOUS mode batches requests continuously.  A step is one launch of the batched kernel
+// (sx_batch.cu) over a list of pieces: for every active request a range of its current phase
+// (phase 0 constructs x and y, phase 1 runs the operation; a request never has both phases in
+// one step, so stream order keeps the phases in order).  The step's byte budget is shared out by
+// water-filling: requests with less remaining work than the fair share finish in this step, the
+// rest split what is left.  Up to steps_in_flight steps are queued on the stream; the thread
+// builds the next step while the GPU runs the previous ones, admits new arrivals between
+// steps, and marks a request DONE when the step holding its last piece has completed.
+//
+// FIFO mode is the per-call baseline: each admitted request is enqueued at once as its own
+// launches (construct x, construct y, operation) in arrival order, like a client calling the
+// algorithms directly.
+//
+// All waits are on the host (event queries, condition variables); no kernel waits on another.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
 #include "sx_internal.h"
+
+namespace sx {
+namespace {
+
+constexpr size_t kAlign = 256;
+
+// First-fit allocator over [0, size) with an address-ordered, coalescing free list.
+class Arena {
+  public:
+    explicit Arena(size_t size) : size_(size) {
+        if (size) free_[0] = size;
+    }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = (bytes + kAlign - 1) / kAlign * kAlign;
+        if (bytes == 0) bytes = kAlign;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                used_ += bytes;
+                peak_ = std::max(peak_, used_);
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + kAlign - 1) / kAlign * kAlign;
+        if (bytes == 0) bytes = kAlign;
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+    size_t peak() const { return peak_; }
+    size_t size() const { return size_; }
+
+  private:
+    size_t size_;
+    size_t used_ = 0, peak_ = 0;
+    std::map<size_t, size_t> free_;
+};
+
+struct Request {
+    uint64_t id = 0;
+    sx_request r{};
+    int state = SX_REQ_QUEUED;
+    int status = SX_OK;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int narr = 0;             // arrays held: x (and y), out
+    size_t off[3] = {0, 0, 0};
+    size_t bytes[3] = {0, 0, 0};
+    bool allocated = false;
+    int phase = 0;            // 0: construct inputs, 1: operation, 2: all work launched
+    uint64_t next = 0;        // next element of the current phase
+    int bypassed = 0;         // admission: times a later request was admitted first
+};
+
+bool has_y(int op) { return op == SX_OP_ADD || op == SX_OP_TRIAD; }
+
+// STREAM byte count of a phase per element.
+size_t phase_bytes_per_elem(const Request &q, int phase) {
+    const size_t es = dtype_size(q.r.dtype);
+    if (phase == 0) return (has_y(q.r.op) ? 2 : 1) * es;
+    return (size_t)op_arrays(q.r.op) * es;
+}
+
+struct Step {
+    int slot = -1;                    // CONTINUOUS: staging slot; FIFO: -1
+    cudaEvent_t ev = nullptr;         // FIFO: the request's completion event
+    std::vector<Request *> finishing; // requests whose last work is in this step
+    uint64_t bytes = 0;
+    double t_launch = 0;
+};
+
+}  // namespace
+}  // namespace sx
 
 using namespace sx;
 
-extern "C" {
-int sx_server_create(sx_target *, const sx_server_cfg *, sx_server **) { return fail(SX_ERR_STATE, "not available"); }
-int sx_server_submit(sx_server *, const sx_request *, uint64_t *) { return fail(SX_ERR_STATE, "not available"); }
-int sx_server_poll(sx_server *, uint64_t, sx_request_status *) { return fail(SX_ERR_STATE, "not available"); }
-int sx_server_wait(sx_server *, uint64_t, int64_t, sx_request_status *) { return fail(SX_ERR_STATE, "not available"); }
-int sx_server_read(sx_server *, uint64_t, int, void *, size_t) { return fail(SX_ERR_STATE, "not available"); }
-int sx_server_release(sx_server *, uint64_t) { return fail(SX_ERR_STATE, "not available"); }
-int sx_server_stats_get(sx_server *, sx_server_stats *) { return fail(SX_ERR_STATE, "not available"); }
-int sx_server_destroy(sx_server *) { return fail(SX_ERR_STATE, "not available"); }
+struct sx_server {
+    sx_target *t = nullptr;
+    sx_server_cfg cfg{};
+    sx_batch_cfg kcfg{};
+    char *base = nullptr;
+    std::unique_ptr<Arena> arena;
+    cudaStream_t read_stream = nullptr;
+
+    std::mutex mu;
+    std::condition_variable cv;       // wakes the server thread
+    std::condition_variable done_cv;  // wakes waiters
+    std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+    std::deque<Request *> waiting;
+    std::vector<Request *> active;
+    std::deque<Step> inflight;
+    std::vector<StepSlot> slots;
+    std::vector<int> free_slots;
+    std::vector<cudaEvent_t> free_events;
+    uint64_t next_id = 1;
+    bool stop = false;
+    int error = SX_OK;
+    std::string error_msg;
+    sx_server_stats stats{};
+    double busy_since = -1;
+
+    std::thread th;
+    std::vector<std::thread> replayers;
+};
+
+namespace sx {
+namespace {
+
+void release_arrays(sx_server *s, Request *q) {
+    if (!q->allocated) return;
+    for (int k = 0; k < 3; ++k)
+        if (q->bytes[k]) s->arena->release(q->off[k], q->bytes[k]);
+    q->allocated = false;
+    s->stats.arena_used = s->arena->used();
 }
+
+void *ptr_of(sx_server *s, const Request *q, int k) { return q->bytes[k] ? s->base + q->off[k] : nullptr; }
+
+// Arena bytes of a request: x, y (ADD/TRIAD), out.
+void request_sizes(const sx_request &r, size_t bytes[3]) {
+    const size_t b = (size_t)r.n * dtype_size(r.dtype);
+    bytes[0] = b;
+    bytes[1] = has_y(r.op) ? b : 0;
+    bytes[2] = b;
+}
+
+size_t rounded_total(const size_t bytes[3]) {
+    size_t t = 0;
+    for (int k = 0; k < 3; ++k)
+        if (bytes[k]) t += std::max<size_t>(kAlign, (bytes[k] + kAlign - 1) / kAlign * kAlign);
+    return t;
+}
+
+bool try_admit(sx_server *s, Request *q) {
+    size_t bytes[3];
+    request_sizes(q->r, bytes);
+    size_t off[3] = {0, 0, 0};
+    int k = 0;
+    for (; k < 3; ++k) {
+        if (!bytes[k]) continue;
+        if (!s->arena->alloc(bytes[k], &off[k])) break;
+    }
+    if (k < 3) {
+        for (int j = 0; j < k; ++j)
+            if (bytes[j]) s->arena->release(off[j], bytes[j]);
+        return false;
+    }
+    for (int j = 0; j < 3; ++j) {
+        q->off[j] = off[j];
+        q->bytes[j] = bytes[j];
+    }
+    q->allocated = true;
+    q->state = SX_REQ_ACTIVE;
+    q->t_admit = now_seconds();
+    q->phase = 0;
+    q->next = 0;
+    s->stats.admitted++;
+    s->stats.arena_used = s->arena->used();
+    s->stats.arena_peak = s->arena->peak();
+    return true;
+}
+
+// Admission in arrival order; a later request may pass one that does not fit, but a request
+// passed 64 times blocks the queue until it fits (no starvation).
+void admit(sx_server *s) {
+    const size_t slots = (size_t)s->cfg.max_active;
+    std::vector<Request *> passed;  // waiting requests a later one may overtake in this pass
+    for (auto it = s->waiting.begin(); it != s->waiting.end();) {
+        if (s->active.size() >= slots) break;
+        Request *q = *it;
+        if (try_admit(s, q)) {
+            for (Request *p : passed) p->bypassed++;
+            s->active.push_back(q);
+            it = s->waiting.erase(it);
+            continue;
+        }
+        if (q->bypassed >= 64) break;  // it has waited long enough: nobody passes it any more
+        passed.push_back(q);
+        ++it;
+    }
+}
+
+int enqueue_fifo(sx_server *s, Request *q, Step &st) {
+    cudaStream_t sm = s->t->stream;
+    const sx_request &r = q->r;
+    SX_TRY(launch_seed(sm, r.dtype, ptr_of(s, q, 0), r.n, r.seed_x, r.lo, r.hi, 0));
+    if (has_y(r.op)) SX_TRY(launch_seed(sm, r.dtype, ptr_of(s, q, 1), r.n, r.seed_y, r.lo, r.hi, 0));
+    const sx_launch_cfg c = resolve_cfg(s->t, r.op, r.dtype, r.n, nullptr);
+    SX_TRY(validate_cfg(s->t, r.op, c));
+    SX_TRY(launch_stream_op(s->t, sm, r.op, r.dtype, ptr_of(s, q, 0), ptr_of(s, q, 1), ptr_of(s, q, 2), r.n, r.q, c));
+    if (s->free_events.empty()) {
+        cudaEvent_t ev;
+        SX_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        s->free_events.push_back(ev);
+    }
+    st.ev = s->free_events.back();
+    s->free_events.pop_back();
+    SX_CUDA(cudaEventRecord(st.ev, sm));
+    st.finishing.push_back(q);
+    st.bytes = (uint64_t)(phase_bytes_per_elem(*q, 0) + phase_bytes_per_elem(*q, 1)) * r.n;
+    q->phase = 2;
+    return SX_OK;
+}
+
+// Build and launch one CONTINUOUS step from the active requests' pending work.
+int launch_step(sx_server *s, bool *launched) {
+    *launched = false;
+    struct Want {
+        Request *q;
+        uint64_t bytes;  // remaining bytes of the current phase
+    };
+    std::vector<Want> w;
+    for (Request *q : s->active)
+        if (q->phase < 2) w.push_back({q, (uint64_t)(q->r.n - q->next) * phase_bytes_per_elem(*q, q->phase)});
+    if (w.empty()) return SX_OK;
+    std::sort(w.begin(), w.end(), [](const Want &a, const Want &b) { return a.bytes < b.bytes; });
+    const int slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    std::vector<sx_batch_item> items;
+    Step st;
+    st.slot = slot;
+    uint64_t budget = (uint64_t)(uint32_t)s->cfg.chunk_bytes;
+    for (size_t i = 0; i < w.size(); ++i) {
+        Request *q = w[i].q;
+        const uint64_t share = budget / (w.size() - i);
+        const uint64_t per = phase_bytes_per_elem(*q, q->phase);
+        uint64_t elems = share / per;
+        elems = std::max<uint64_t>(elems / 64 * 64, 64);  // whole 64-element units, at least one
+        const uint64_t remaining = q->r.n - q->next;
+        if (elems >= remaining) elems = remaining;
+        const uint64_t lo = q->next, hi = lo + elems;
+        const sx_request &r = q->r;
+        const size_t es = dtype_size(r.dtype);
+        if (q->phase == 0) {
+            sx_batch_item it{};
+            it.op = SX_OP_SEED;
+            it.dtype = r.dtype;
+            it.n = elems;
+            it.out = (char *)ptr_of(s, q, 0) + lo * es;
+            it.q = r.lo;
+            it.q2 = r.hi;
+            it.seed = r.seed_x;
+            it.index_base = lo;
+            items.push_back(it);
+            if (has_y(r.op)) {
+                it.out = (char *)ptr_of(s, q, 1) + lo * es;
+                it.seed = r.seed_y;
+                items.push_back(it);
+            }
+        } else {
+            sx_batch_item it{};
+            it.op = r.op;
+            it.dtype = r.dtype;
+            it.n = elems;
+            it.x = (const char *)ptr_of(s, q, 0) + lo * es;
+            it.y = has_y(r.op) ? (const char *)ptr_of(s, q, 1) + lo * es : nullptr;
+            it.out = (char *)ptr_of(s, q, 2) + lo * es;
+            it.q = r.q;
+            items.push_back(it);
+        }
+        st.bytes += elems * per;
+        budget -= std::min(budget, elems * per);
+        q->next = hi;
+        if (q->next == r.n) {
+            q->next = 0;
+            q->phase++;
+            if (q->phase == 2) st.finishing.push_back(q);
+        }
+    }
+    const int rc = step_launch(s->t, s->t->stream, s->slots[slot], items.data(), items.size(), s->kcfg);
+    if (rc != SX_OK) {
+        s->free_slots.push_back(slot);
+        return rc;
+    }
+    st.t_launch = now_seconds();
+    s->inflight.push_back(std::move(st));
+    s->stats.steps++;
+    s->stats.launches++;
+    *launched = true;
+    return SX_OK;
+}
+
+// Retire completed steps from the front of the in-flight queue.  Returns true if any retired.
+bool retire(sx_server *s) {
+    bool any = false;
+    while (!s->inflight.empty()) {
+        Step &st = s->inflight.front();
+        cudaEvent_t ev = st.slot >= 0 ? s->slots[st.slot].done : st.ev;
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) {
+            s->error = SX_ERR_CUDA;
+            s->error_msg = cudaGetErrorString(e);
+        }
+        const double now = now_seconds();
+        for (Request *q : st.finishing) {
+            q->state = SX_REQ_DONE;
+            q->t_done = now;
+            s->stats.completed++;
+            s->active.erase(std::find(s->active.begin(), s->active.end(), q));
+            if (q->r.flags & SX_REQ_AUTO_RELEASE) release_arrays(s, q);
+        }
+        s->stats.bytes_moved += st.bytes;
+        if (st.slot >= 0) s->free_slots.push_back(st.slot);
+        else s->free_events.push_back(st.ev);
+        s->inflight.pop_front();
+        any = true;
+    }
+    return any;
+}
+
+void server_loop(sx_server *s) {
+    DeviceScope ds(s->t->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    const bool fifo = s->cfg.mode == SX_SERVE_FIFO;
+    for (;;) {
+        const bool retired = retire(s);
+        if (retired) s->done_cv.notify_all();
+        if (!s->stop) admit(s);
+        bool launched = false;
+        if (s->error == SX_OK) {
+            int rc = SX_OK;
+            if (fifo) {
+                for (Request *q : s->active) {
+                    if (q->phase != 0) continue;
+                    Step st;
+                    rc = enqueue_fifo(s, q, st);
+                    if (rc != SX_OK) break;
+                    st.t_launch = now_seconds();
+                    s->inflight.push_back(std::move(st));
+                    s->stats.launches += has_y(q->r.op) ? 3 : 2;
+                    launched = true;
+                }
+            } else if (!s->free_slots.empty()) {
+                rc = launch_step(s, &launched);
+            }
+            if (rc != SX_OK) {
+                s->error = rc;
+                s->error_msg = sx_last_error();
+            }
+        }
+        const double now = now_seconds();
+        if (!s->inflight.empty()) {
+            if (s->busy_since < 0) s->busy_since = now;
+        } else if (s->busy_since >= 0) {
+            s->stats.busy_seconds += now - s->busy_since;
+            s->busy_since = -1;
+        }
+        const bool work_pending = !s->active.empty() || !s->inflight.empty();
+        if (s->stop && !work_pending) break;
+        if (s->stop && s->error != SX_OK && s->inflight.empty()) break;
+        if (launched || retired) continue;
+        if (!s->inflight.empty()) {
+            // GPU busy: poll its completion without holding the lock
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
+        } else {
+            s->cv.wait_for(lk, std::chrono::milliseconds(5));
+        }
+    }
+    // reject what never got in
+    for (Request *q : s->waiting) {
+        q->state = SX_REQ_REJECTED;
+        q->status = SX_ERR_STATE;
+    }
+    s->waiting.clear();
+    s->done_cv.notify_all();
+}
+
+void fill_status(sx_server *s, const Request *q, sx_request_status *st) {
+    st->state = q->state;
+    st->status = q->status;
+    st->t_submit = q->t_submit;
+    st->t_admit = q->t_admit;
+    st->t_done = q->t_done;
+    const bool live = q->allocated;
+    st->x = live ? ptr_of(s, q, 0) : nullptr;
+    st->y = live ? ptr_of(s, q, 1) : nullptr;
+    st->out = live ? ptr_of(s, q, 2) : nullptr;
+}
+
+int check_request(const sx_request *r) {
+    if (!r) return fail(SX_ERR_INVALID, "request is NULL");
+    if (r->op < SX_OP_COPY || r->op > SX_OP_TRIAD) return fail(SX_ERR_INVALID, "request op %d", r->op);
+    if (r->dtype != SX_F32 && r->dtype != SX_F64) return fail(SX_ERR_DTYPE, "request dtype %d", r->dtype);
+    if (r->n == 0) return fail(SX_ERR_INVALID, "request of zero elements");
+    if (r->n > (1ull << 40)) return fail(SX_ERR_INVALID, "request too large");
+    return SX_OK;
+}
+
+// Register a request (lock held).  Oversized requests are rejected at once.
+void submit_locked(sx_server *s, const sx_request &r, uint64_t id, double t) {
+    auto q = std::make_unique<Request>();
+    q->id = id;
+    q->r = r;
+    q->t_submit = t;
+    size_t bytes[3];
+    request_sizes(r, bytes);
+    s->stats.submitted++;
+    Request *raw = q.get();
+    s->reqs[id] = std::move(q);
+    if (rounded_total(bytes) > s->arena->size()) {
+        raw->state = SX_REQ_REJECTED;
+        raw->status = SX_ERR_OOM;
+        s->stats.rejected++;
+        s->done_cv.notify_all();
+        return;
+    }
+    s->waiting.push_back(raw);
+}
+
+Request *find(sx_server *s, uint64_t id) {
+    auto it = s->reqs.find(id);
+    return it == s->reqs.end() ? nullptr : it->second.get();
+}
+
+}  // namespace
+}  // namespace sx
+
+extern "C" {
+
+int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out) {
+    if (!t || !cfg || !out) return fail(SX_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    sx_server_cfg c = *cfg;
+    if (c.mode != SX_SERVE_CONTINUOUS && c.mode != SX_SERVE_FIFO) return fail(SX_ERR_INVALID, "mode %d", c.mode);
+    if (c.budget_bytes == 0) return fail(SX_ERR_INVALID, "budget_bytes must be positive");
+    if (c.max_active == 0) c.max_active = 256;
+    if (c.chunk_bytes == 0) c.chunk_bytes = 256 << 20;
+    if (c.steps_in_flight == 0) c.steps_in_flight = 3;
+    if (c.max_active < 1 || c.max_active > 65536) return fail(SX_ERR_INVALID, "max_active %d", c.max_active);
+    if (c.chunk_bytes < (1 << 20)) return fail(SX_ERR_INVALID, "chunk_bytes %d below 1 MiB", c.chunk_bytes);
+    if (c.steps_in_flight < 1 || c.steps_in_flight > 8) return fail(SX_ERR_INVALID, "steps_in_flight %d", c.steps_in_flight);
+    sx_batch_cfg k{};
+    k.chunk_bytes = c.tile_bytes ? c.tile_bytes : 256 * 1024;
+    k.threads = c.threads ? c.threads : 512;
+    k.blocks_per_sm = c.blocks_per_sm ? c.blocks_per_sm : 4;
+    k.vec_bytes = c.vec_bytes ? c.vec_bytes : 32;
+    if (k.chunk_bytes < 16384 || k.threads % 32 || k.threads < 64 || k.threads > 1024 ||
+        k.blocks_per_sm * k.threads > 2048 || (k.vec_bytes != 16 && k.vec_bytes != 32))
+        return fail(SX_ERR_INVALID, "batched-kernel shape (tile %d, threads %d, blocks/SM %d, vec %d)",
+                    k.chunk_bytes, k.threads, k.blocks_per_sm, k.vec_bytes);
+    // the arena is charged to the target's budget like any allocation
+    size_t used = t->used.load();
+    do {
+        if (used + c.budget_bytes > t->budget)
+            return fail(SX_ERR_OOM, "server arena of %llu bytes exceeds the target budget",
+                        (unsigned long long)c.budget_bytes);
+    } while (!t->used.compare_exchange_weak(used, used + c.budget_bytes));
+    DeviceScope ds(t->device);
+    sx_server *s = new (std::nothrow) sx_server();
+    if (!s) {
+        t->used -= c.budget_bytes;
+        return fail(SX_ERR_OOM, "host allocation failed");
+    }
+    s->t = t;
+    s->cfg = c;
+    s->kcfg = k;
+    cudaError_t e = cudaMalloc(&s->base, c.budget_bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->read_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        if (s->base) cudaFree(s->base);
+        t->used -= c.budget_bytes;
+        delete s;
+        cudaGetLastError();
+        if (e == cudaErrorMemoryAllocation) return fail(SX_ERR_OOM, "arena allocation failed");
+        return cuda_fail(e, "server setup");
+    }
+    s->arena.reset(new Arena(c.budget_bytes));
+    s->stats.arena_bytes = c.budget_bytes;
+    if (c.mode == SX_SERVE_CONTINUOUS) {
+        s->slots.resize(c.steps_in_flight);
+        for (int i = c.steps_in_flight - 1; i >= 0; --i) s->free_slots.push_back(i);
+    }
+    s->th = std::thread(server_loop, s);
+    *out = s;
+    return SX_OK;
+}
+
+int sx_server_submit(sx_server *s, const sx_request *r, uint64_t *id) {
+    if (!s || !id) return fail(SX_ERR_INVALID, "NULL argument");
+    SX_TRY(check_request(r));
+    const double t = now_seconds();
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (s->stop) return fail(SX_ERR_STATE, "server is stopping");
+        *id = s->next_id++;
+        submit_locked(s, *r, *id, t);
+    }
+    s->cv.notify_one();
+    return SX_OK;
+}
+
+int sx_server_replay(sx_server *s, const sx_request *reqs, const double *t_arrival, size_t count,
+                     uint64_t *ids) {
+    if (!s || (count && (!reqs || !t_arrival || !ids))) return fail(SX_ERR_INVALID, "NULL argument");
+    for (size_t k = 0; k < count; ++k) {
+        SX_TRY(check_request(&reqs[k]));
+        if (k && t_arrival[k] < t_arrival[k - 1]) return fail(SX_ERR_INVALID, "arrival times must not decrease");
+    }
+    uint64_t first;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (s->stop) return fail(SX_ERR_STATE, "server is stopping");
+        first = s->next_id;
+        s->next_id += count;
+    }
+    for (size_t k = 0; k < count; ++k) ids[k] = first + k;
+    std::vector<sx_request> rs(reqs, reqs + count);
+    std::vector<double> ts(t_arrival, t_arrival + count);
+    const double t0 = now_seconds();
+    std::lock_guard<std::mutex> g(s->mu);
+    s->replayers.emplace_back([s, rs = std::move(rs), ts = std::move(ts), first, t0]() {
+        for (size_t k = 0; k < rs.size(); ++k) {
+            const double due = t0 + ts[k];
+            for (;;) {
+                const double now = now_seconds();
+                if (now >= due) break;
+                if (due - now > 2e-4)
+                    std::this_thread::sleep_for(std::chrono::duration<double>(due - now - 1e-4));
+                else
+                    std::this_thread::yield();
+            }
+            {
+                std::lock_guard<std::mutex> g2(s->mu);
+                submit_locked(s, rs[k], first + k, now_seconds());
+            }
+            s->cv.notify_one();
+        }
+    });
+    return SX_OK;
+}
+
+int sx_server_poll(sx_server *s, uint64_t id, sx_request_status *st) {
+    if (!s || !st) return fail(SX_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> g(s->mu);
+    Request *q = find(s, id);
+    if (!q) return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
+    fill_status(s, q, st);
+    return SX_OK;
+}
+
+int sx_server_wait(sx_server *s, uint64_t id, int64_t timeout_ms, sx_request_status *st) {
+    if (!s) return fail(SX_ERR_INVALID, "NULL argument");
+    std::unique_lock<std::mutex> lk(s->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    for (;;) {
+        Request *q = find(s, id);
+        if (!q) {
+            // a replayed request may not be registered yet
+            if (id >= s->next_id) return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
+        } else if (q->state == SX_REQ_DONE || q->state == SX_REQ_REJECTED || q->state == SX_REQ_RELEASED) {
+            if (st) fill_status(s, q, st);
+            return SX_OK;
+        }
+        if (s->error != SX_OK) return fail(s->error, "server failed: %s", s->error_msg.c_str());
+        if (timeout_ms < 0) {
+            s->done_cv.wait_for(lk, std::chrono::milliseconds(50));
+        } else {
+            if (std::chrono::steady_clock::now() >= deadline)
+                return fail(SX_ERR_TIMEOUT, "request %llu not done after %lld ms", (unsigned long long)id,
+                            (long long)timeout_ms);
+            s->done_cv.wait_until(lk, std::min(deadline, std::chrono::steady_clock::now() + std::chrono::milliseconds(50)));
+        }
+    }
+}
+
+int sx_server_read(sx_server *s, uint64_t id, int which, void *host, size_t n) {
+    if (!s || (!host && n)) return fail(SX_ERR_INVALID, "NULL argument");
+    if (which < 0 || which > 2) return fail(SX_ERR_INVALID, "which=%d: 0 = x, 1 = y, 2 = out", which);
+    const void *src;
+    size_t bytes;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        Request *q = find(s, id);
+        if (!q) return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
+        if (q->state != SX_REQ_DONE || !q->allocated) return fail(SX_ERR_STATE, "request %llu has no resident result", (unsigned long long)id);
+        if (!q->bytes[which]) return fail(SX_ERR_INVALID, "request %llu has no array %d", (unsigned long long)id, which);
+        if (n > q->r.n) return fail(SX_ERR_INVALID, "n=%zu exceeds the request length", n);
+        src = ptr_of(s, q, which);
+        bytes = n * dtype_size(q->r.dtype);
+    }
+    DeviceScope ds(s->t->device);
+    SX_CUDA(cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, s->read_stream));
+    SX_CUDA(cudaStreamSynchronize(s->read_stream));
+    return SX_OK;
+}
+
+int sx_server_release(sx_server *s, uint64_t id) {
+    if (!s) return fail(SX_ERR_INVALID, "NULL argument");
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        Request *q = find(s, id);
+        if (!q) return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
+        if (q->state != SX_REQ_DONE && q->state != SX_REQ_REJECTED)
+            return fail(SX_ERR_STATE, "request %llu is not finished", (unsigned long long)id);
+        release_arrays(s, q);
+        if (q->state == SX_REQ_DONE) q->state = SX_REQ_RELEASED;
+    }
+    s->cv.notify_one();  // memory freed: admission may proceed
+    return SX_OK;
+}
+
+int sx_server_stats_get(sx_server *s, sx_server_stats *st) {
+    if (!s || !st) return fail(SX_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> g(s->mu);
+    *st = s->stats;
+    st->arena_used = s->arena->used();
+    st->arena_peak = s->arena->peak();
+    if (s->busy_since >= 0) st->busy_seconds += now_seconds() - s->busy_since;
+    return SX_OK;
+}
+
+int sx_server_destroy(sx_server *s) {
+    if (!s) return fail(SX_ERR_INVALID, "NULL argument");
+    std::vector<std::thread> reps;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        reps.swap(s->replayers);
+    }
+    for (auto &r : reps) r.join();  // every replayed request is submitted
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->th.joinable()) s->th.join();
+    const int err = s->error;
+    const std::string msg = s->error_msg;
+    {
+        DeviceScope ds(s->t->device);
+        cudaStreamSynchronize(s->t->stream);
+        for (auto &sl : s->slots) step_slot_free(sl);
+        for (auto ev : s->free_events) cudaEventDestroy(ev);
+        if (s->read_stream) cudaStreamDestroy(s->read_stream);
+        cudaFree(s->base);
+    }
+    s->t->used -= s->cfg.budget_bytes;
+    delete s;
+    if (err != SX_OK) return fail(err, "server stopped after an error: %s", msg.c_str());
+    return SX_OK;
+}
+
+}  // extern "C"

@@ -28,6 +28,7 @@ SX_VARIANT_AUTO, SX_VARIANT_VECTOR, SX_VARIANT_BULK = 0, 1, 2
 SX_FN_TO_UPPER, SX_FN_TO_LOWER = 1, 2
 SX_SERVE_CONTINUOUS, SX_SERVE_FIFO = 0, 1
 SX_REQ_QUEUED, SX_REQ_ACTIVE, SX_REQ_DONE, SX_REQ_REJECTED, SX_REQ_RELEASED = 0, 1, 2, 3, 4
+SX_REQ_AUTO_RELEASE = 1
 
 OPS = {"copy": SX_OP_COPY, "scale": SX_OP_SCALE, "add": SX_OP_ADD, "triad": SX_OP_TRIAD,
        "seed": SX_OP_SEED}
@@ -76,13 +77,13 @@ class sx_server_cfg(C.Structure):
     _fields_ = [("budget_bytes", C.c_uint64), ("mode", C.c_int32), ("max_active", C.c_int32),
                 ("chunk_bytes", C.c_int32), ("steps_in_flight", C.c_int32),
                 ("threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("vec_bytes", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("tile_bytes", C.c_int32)]
 
 
 class sx_request(C.Structure):
     _fields_ = [("op", C.c_int32), ("dtype", C.c_int32), ("n", C.c_uint64), ("q", C.c_double),
                 ("seed_x", C.c_uint64), ("seed_y", C.c_uint64), ("lo", C.c_double),
-                ("hi", C.c_double)]
+                ("hi", C.c_double), ("flags", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class sx_request_status(C.Structure):
@@ -156,6 +157,7 @@ _PROTOS = {
     "sx_tune_clear": [],
     "sx_server_create": [P, C.POINTER(sx_server_cfg), PP],
     "sx_server_submit": [P, C.POINTER(sx_request), C.POINTER(C.c_uint64)],
+    "sx_server_replay": [P, C.POINTER(sx_request), C.POINTER(C.c_double), SZ, C.POINTER(C.c_uint64)],
     "sx_server_poll": [P, U64, C.POINTER(sx_request_status)],
     "sx_server_wait": [P, U64, C.c_int64, C.POINTER(sx_request_status)],
     "sx_server_read": [P, U64, I, P, SZ],
@@ -464,11 +466,23 @@ def sx_server_create(t, **cfg):
 
 
 def sx_server_submit(s, op: int, dtype: int, n: int, q: float = 3.0, seed_x: int = 1,
-                     seed_y: int = 2, lo: float = -1.0, hi: float = 1.0) -> int:
-    r = sx_request(op=op, dtype=dtype, n=n, q=q, seed_x=seed_x, seed_y=seed_y, lo=lo, hi=hi)
+                     seed_y: int = 2, lo: float = -1.0, hi: float = 1.0, flags: int = 0) -> int:
+    r = sx_request(op=op, dtype=dtype, n=n, q=q, seed_x=seed_x, seed_y=seed_y, lo=lo, hi=hi,
+                   flags=flags)
     rid = C.c_uint64()
     _check(lib.sx_server_submit(s, C.byref(r), C.byref(rid)), "sx_server_submit")
     return rid.value
+
+
+def sx_server_replay(s, requests, t_arrival) -> list:
+    """Submit `requests` (sx_request or dicts) at `t_arrival` seconds from now, from a library
+    thread; returns their ids at once."""
+    k = len(requests)
+    reqs = (sx_request * k)(*[r if isinstance(r, sx_request) else sx_request(**r) for r in requests])
+    ts = (C.c_double * k)(*t_arrival)
+    ids = (C.c_uint64 * k)()
+    _check(lib.sx_server_replay(s, reqs, ts, k, ids), "sx_server_replay")
+    return list(ids)
 
 
 def _status_dict(st: sx_request_status) -> dict:

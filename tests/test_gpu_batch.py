@@ -79,7 +79,7 @@ class Workload:
             dt, n = s["dt"], s["n"]
             r = s["regions"][2]
             got = h[r:r + n * np.dtype(dt).itemsize].view(dt)
-            x, y = self.host_in[k]
+            x, y = self.host_in[k][0][:n], self.host_in[k][1][:n]
             if s["op"] == sx.SX_OP_SEED:
                 want = si.uniform(s["seed"], n, dt, -1.0, 1.0, start=s["base"])
             else:

@@ -1,0 +1,142 @@
+"""GPU tests of the serving loop: every request's inputs and result are bit-identical to the
+request run alone and to the oracle, in continuous-batching and per-call FIFO modes, under
+admission pressure; requests that arrive while others run overlap with them."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2206_06302_b300 as sx
+import stream_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+OPN = {sx.SX_OP_COPY: "copy", sx.SX_OP_SCALE: "scale", sx.SX_OP_ADD: "add", sx.SX_OP_TRIAD: "triad"}
+NP = {sx.SX_F32: np.float32, sx.SX_F64: np.float64}
+
+
+def _requests(count, seed, lo_exp=4, hi_exp=18):
+    ops = [sx.SX_OP_COPY, sx.SX_OP_SCALE, sx.SX_OP_ADD, sx.SX_OP_TRIAD]
+    lens = si.log_uniform_lengths(si.word_scalar(seed, 1), count, lo_exp, hi_exp)
+    out = []
+    for k in range(count):
+        out.append(dict(op=ops[k % 4], dtype=sx.SX_F64 if (k // 4) % 2 == 0 else sx.SX_F32,
+                        n=int(lens[k]), q=[3.0, -0.25, 1.0 / 3.0][k % 3],
+                        seed_x=int(si.word_scalar(seed, 100 + 2 * k)),
+                        seed_y=int(si.word_scalar(seed, 101 + 2 * k)), lo=-1.0, hi=1.0))
+    return out
+
+
+def _read(s, rid, which, r):
+    dt = NP[r["dtype"]]
+    h = np.empty(r["n"], dt)
+    sx.sx_server_read(s, rid, which, h.ctypes.data, r["n"])
+    return h
+
+
+def _expected(r):
+    dt = NP[r["dtype"]]
+    x = si.uniform(r["seed_x"], r["n"], dt, r["lo"], r["hi"])
+    y = si.uniform(r["seed_y"], r["n"], dt, r["lo"], r["hi"])
+    return x, y, oracle.apply(OPN[r["op"]], x, y, r["q"])
+
+
+def _check_all(s, ids, reqs, what):
+    for rid, r in zip(ids, reqs):
+        st = sx.sx_server_wait(s, rid, 60000)
+        assert st["state"] == sx.SX_REQ_DONE, (what, rid, st)
+        x, y, want = _expected(r)
+        got = _read(s, rid, 2, r)
+        assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), (what, rid, r)
+        assert np.array_equal(_read(s, rid, 0, r).view(np.uint8), x.view(np.uint8)), (what, rid)
+        if r["op"] in (sx.SX_OP_ADD, sx.SX_OP_TRIAD):
+            assert np.array_equal(_read(s, rid, 1, r).view(np.uint8), y.view(np.uint8)), (what, rid)
+        sx.sx_server_release(s, rid)
+
+
+@pytest.mark.parametrize("mode", [sx.SX_SERVE_CONTINUOUS, sx.SX_SERVE_FIFO])
+def test_each_request_alone(target, mode):
+    s = sx.sx_server_create(target, budget_bytes=1 << 30, mode=mode)
+    reqs = _requests(8, seed=3, lo_exp=16, hi_exp=17)
+    for r in reqs:
+        rid = sx.sx_server_submit(s, **r)
+        _check_all(s, [rid], [r], "alone")
+    sx.sx_server_destroy(s)
+
+
+@pytest.mark.parametrize("mode", [sx.SX_SERVE_CONTINUOUS, sx.SX_SERVE_FIFO])
+def test_mix_equals_alone(target, mode):
+    """200 requests of mixed op, type and length arrive together; small step budget and tiles
+    make long requests span many steps and share them with short ones."""
+    reqs = _requests(200, seed=4)
+    s = sx.sx_server_create(target, budget_bytes=256 << 20, mode=mode, chunk_bytes=1 << 20,
+                            tile_bytes=16384, max_active=64, steps_in_flight=2)
+    ids = [sx.sx_server_submit(s, **r) for r in reqs]
+    _check_all(s, ids, reqs, "mix")
+    st = sx.sx_server_stats_get(s)
+    assert st["completed"] == 200 and st["rejected"] == 0
+    assert st["arena_peak"] <= 256 << 20
+    if mode == sx.SX_SERVE_CONTINUOUS:
+        assert st["steps"] > 1
+    sx.sx_server_destroy(s)
+
+
+def test_replayed_poisson_stream(target):
+    reqs = _requests(150, seed=5)
+    arr = si.poisson_requests(5, 150, rate_per_s=20000.0)
+    t = [a["t"] for a in arr]
+    s = sx.sx_server_create(target, budget_bytes=512 << 20, chunk_bytes=4 << 20)
+    ids = sx.sx_server_replay(s, [sx.sx_request(**r) for r in reqs], t)
+    _check_all(s, ids, reqs, "replay")
+    sx.sx_server_destroy(s)
+
+
+def test_admission_waits_for_memory_and_rejects_oversize(target):
+    # each request holds 3 arrays of 1 MiB (F64, n = 2^17): at most 2 fit in an 8 MiB arena
+    n = 1 << 17
+    s = sx.sx_server_create(target, budget_bytes=8 << 20, chunk_bytes=1 << 20)
+    reqs = [dict(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=n, q=3.0, seed_x=10 + k, seed_y=20 + k,
+                 lo=-1.0, hi=1.0, flags=sx.SX_REQ_AUTO_RELEASE) for k in range(10)]
+    ids = [sx.sx_server_submit(s, **r) for r in reqs]
+    big = sx.sx_server_submit(s, op=sx.SX_OP_COPY, dtype=sx.SX_F64, n=1 << 20)  # 16 MiB > arena
+    st = sx.sx_server_poll(s, big)
+    assert st["state"] == sx.SX_REQ_REJECTED and st["status"] == sx.SX_ERR_OOM
+    for rid in ids:
+        st = sx.sx_server_wait(s, rid, 60000)
+        assert st["state"] == sx.SX_REQ_DONE and st["out"] is None  # auto-released
+    stats = sx.sx_server_stats_get(s)
+    assert stats["completed"] == 10 and stats["rejected"] == 1
+    assert stats["arena_peak"] <= 8 << 20 and stats["arena_used"] == 0
+    sx.sx_server_destroy(s)
+
+
+def test_short_requests_overtake_a_long_one(target):
+    """Continuous batching: short requests submitted while a long one runs finish before it;
+    with the per-call FIFO they finish after it."""
+    order = {}
+    for mode in (sx.SX_SERVE_CONTINUOUS, sx.SX_SERVE_FIFO):
+        s = sx.sx_server_create(target, budget_bytes=8 << 30, mode=mode, chunk_bytes=64 << 20)
+        long_id = sx.sx_server_submit(s, op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=1 << 28, q=3.0,
+                                      flags=sx.SX_REQ_AUTO_RELEASE)
+        short = [sx.sx_server_submit(s, op=sx.SX_OP_ADD, dtype=sx.SX_F32, n=1 << 12,
+                                     flags=sx.SX_REQ_AUTO_RELEASE) for _ in range(8)]
+        t_long = sx.sx_server_wait(s, long_id, 60000)["t_done"]
+        t_short = [sx.sx_server_wait(s, r, 60000)["t_done"] for r in short]
+        order[mode] = sum(t < t_long for t in t_short)
+        sx.sx_server_destroy(s)
+    assert order[sx.SX_SERVE_CONTINUOUS] == 8
+    assert order[sx.SX_SERVE_FIFO] == 0
+
+
+def test_bad_calls(target):
+    with pytest.raises(sx.SxError):
+        sx.sx_server_create(target, budget_bytes=0)
+    s = sx.sx_server_create(target, budget_bytes=1 << 20)
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_server_submit(s, op=7, dtype=sx.SX_F64, n=10)
+    assert ei.value.status == sx.SX_ERR_INVALID
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_server_release(s, 12345)
+    assert ei.value.status == sx.SX_ERR_INVALID
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_server_wait(s, 999, 10)
+    sx.sx_server_destroy(s)
