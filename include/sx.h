@@ -285,6 +285,32 @@ int sx_batch_completion_ns(sx_batch *b, uint64_t *t_ns, size_t count);
 int sx_batch_info(const sx_batch *b, sx_batch_cfg *cfg, uint64_t *tiles, uint64_t *bytes);
 int sx_batch_destroy(sx_batch *b);
 
+/* ---- a batch launch that allocates nothing ---------------------------------------------
+ * The paper has no counterpart to this call.  It is for callers that must not allocate device
+ * memory: a process whose device memory already belongs to another allocator (for instance a
+ * framework's caching pool that has reserved the free memory, so cudaMalloc would fail), or a
+ * latency-bound loop that cannot afford cudaMalloc/cudaFree, which may synchronize the whole
+ * device.  It runs `items` once, like sx_batch_create + sx_batch_launch with the same shape,
+ * but needs no target and allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine): the item and tile tables go to a static device array of SX_NOALLOC_SCRATCH_BYTES
+ * that every GPU which loads this library holds until the process exits.
+ *   stream   cudaStream_t to launch on (NULL = the legacy default stream), on the current device
+ *   items    count instances as for sx_batch_create (device pointers, caller-owned); at most
+ *            SX_NOALLOC_MAX_ITEMS items cut into at most SX_NOALLOC_MAX_TILES work tiles of
+ *            cfg->chunk_bytes, else SX_ERR_INVALID before anything is launched
+ *   cfg      launch shape as sx_batch_cfg (NULL or zero fields = 256 KiB tiles, 512 threads,
+ *            4 blocks per SM, 32-byte vectors; the autotuner's table is not consulted)
+ * Returns once the work is enqueued.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream capture.  All
+ * calls share the one array and each overwrites the tables it uses: calls whose work overlaps
+ * on the GPU (different streams, no ordering between them) race and give wrong results;
+ * calls on one stream, or otherwise ordered, are safe.  Calls from several host threads take
+ * turns on a lock. */
+#define SX_NOALLOC_MAX_ITEMS 4096
+#define SX_NOALLOC_MAX_TILES 65536
+#define SX_NOALLOC_SCRATCH_BYTES 884736 /* 4096 items x 88 B + 65536 tiles x 8 B */
+int sx_batch_run_noalloc(void *stream, const sx_batch_item *items, size_t count, const sx_batch_cfg *cfg);
+
 /* ---- autotuner ------------------------------------------------------------------------ */
 /* Time the candidate launch shapes (both variants, vector widths, unroll, block counts,
  * cache hints, bulk tile sizes) for (op, dtype, n) on scratch arrays the tuner allocates on the

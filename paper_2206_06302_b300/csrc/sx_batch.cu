@@ -620,3 +620,93 @@ int sx_tune_batch(sx_batch *b, sx_batch_cfg *best_out, float *ms_out) {
 }
 
 }  // extern "C"
+
+// ---- a batch launch that allocates nothing -------------------------------------------------------
+// Some callers must not allocate device memory: a process whose device memory already belongs
+// to another allocator (a framework's caching pool that has reserved what is free, so
+// cudaMalloc would fail or fragment it), or a latency-bound loop that cannot pay for cudaMalloc
+// and cudaFree, which may synchronize the whole device.  sx_batch_run_noalloc serves them with
+// the same batched kernel as sx_batch_launch, its item and tile tables kept in the static array
+// below instead of in memory allocated per batch.  The array is part of the library's device
+// image, so every GPU that loads the library holds it until the process exits.
+namespace sx {
+namespace {
+
+constexpr size_t kNoAllocMaxItems = SX_NOALLOC_MAX_ITEMS;
+constexpr size_t kNoAllocMaxTiles = SX_NOALLOC_MAX_TILES;
+constexpr size_t kNoAllocItemBytes = kNoAllocMaxItems * sizeof(DevItem);
+constexpr size_t kNoAllocBytes = kNoAllocItemBytes + kNoAllocMaxTiles * sizeof(DevTile);
+static_assert(kNoAllocBytes == SX_NOALLOC_SCRATCH_BYTES, "header states the scratch size");
+static_assert(kNoAllocItemBytes % 256 == 0, "tile table stays 256-byte aligned");
+
+// Device scratch: the item table, then the tile table.  In host code this name is only a
+// stand-in for the symbol; the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Host staging of the tables (static too: the call allocates no host memory either), the
+// per-device scratch addresses, and a lock that makes calls from several threads take turns.
+constexpr int kNoAllocMaxDevices = 64;
+DevItem g_noalloc_host_items[kNoAllocMaxItems];
+DevTile g_noalloc_host_tiles[kNoAllocMaxTiles];
+void *g_noalloc_dev_ptr[kNoAllocMaxDevices];
+int g_noalloc_dev_sms[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// Set-up, once per device, with that device current: look up the scratch's device address.
+int noalloc_setup(int dev) {
+    if (g_noalloc_dev_ptr[dev]) return SX_OK;
+    void *p = nullptr;
+    SX_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    int sms = 0;
+    SX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    g_noalloc_dev_sms[dev] = sms;
+    g_noalloc_dev_ptr[dev] = p;
+    return SX_OK;
+}
+
+}  // namespace
+}  // namespace sx
+
+extern "C" int sx_batch_run_noalloc(void *stream, const sx_batch_item *items, size_t count,
+                                    const sx_batch_cfg *cfg) {
+    if (!items && count) return fail(SX_ERR_INVALID, "items is NULL");
+    if (count > kNoAllocMaxItems)
+        return fail(SX_ERR_INVALID, "%zu items exceed the %zu that the static scratch holds; split the batch",
+                    count, kNoAllocMaxItems);
+    SX_TRY(check_items(items, count));
+    sx_batch_cfg c = cfg ? *cfg : sx_batch_cfg{};
+    if (c.chunk_bytes == 0) c.chunk_bytes = 256 * 1024;
+    if (c.threads == 0) c.threads = 512;
+    if (c.blocks_per_sm == 0) c.blocks_per_sm = 4;
+    if (c.vec_bytes == 0) c.vec_bytes = 32;
+    SX_TRY(validate_batch_cfg(c));
+    const size_t want = count_tiles(items, count, c.chunk_bytes);
+    if (want > kNoAllocMaxTiles)
+        return fail(SX_ERR_INVALID, "the batch needs %zu work tiles but the static scratch holds %zu; "
+                    "raise chunk_bytes or split the batch", want, kNoAllocMaxTiles);
+    int dev = 0;
+    SX_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SX_ERR_INVALID, "device %d out of range", dev);
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    SX_TRY(noalloc_setup(dev));
+    size_t nt = 0;
+    // every call writes the whole part of the tables it uses; nothing is read before written
+    SX_TRY(fill_tables(items, count, c.chunk_bytes, g_noalloc_host_items, g_noalloc_host_tiles,
+                       kNoAllocMaxTiles, &nt, nullptr));
+    if (nt == 0) return SX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *base = static_cast<char *>(g_noalloc_dev_ptr[dev]);
+    DevItem *d_items = reinterpret_cast<DevItem *>(base);
+    DevTile *d_tiles = reinterpret_cast<DevTile *>(base + kNoAllocItemBytes);
+    // copies from pageable host memory: the staging arrays may be refilled once these return
+    SX_CUDA(cudaMemcpyAsync(d_items, g_noalloc_host_items, count * sizeof(DevItem), cudaMemcpyHostToDevice, s));
+    SX_CUDA(cudaMemcpyAsync(d_tiles, g_noalloc_host_tiles, nt * sizeof(DevTile), cudaMemcpyHostToDevice, s));
+    uint64_t grid = (uint64_t)g_noalloc_dev_sms[dev] * c.blocks_per_sm;
+    if (grid > nt) grid = nt;
+    if (c.vec_bytes == 16)
+        k_batch<16><<<(unsigned)grid, c.threads, 0, s>>>(d_items, d_tiles, nt, nullptr, nullptr, nullptr);
+    else
+        k_batch<32><<<(unsigned)grid, c.threads, 0, s>>>(d_items, d_tiles, nt, nullptr, nullptr, nullptr);
+    SX_CUDA(cudaGetLastError());
+    return SX_OK;
+}

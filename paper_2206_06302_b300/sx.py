@@ -29,6 +29,7 @@ SX_FN_TO_UPPER, SX_FN_TO_LOWER = 1, 2
 SX_SERVE_CONTINUOUS, SX_SERVE_FIFO = 0, 1
 SX_REQ_QUEUED, SX_REQ_ACTIVE, SX_REQ_DONE, SX_REQ_REJECTED, SX_REQ_RELEASED = 0, 1, 2, 3, 4
 SX_REQ_AUTO_RELEASE = 1
+SX_NOALLOC_MAX_ITEMS, SX_NOALLOC_MAX_TILES, SX_NOALLOC_SCRATCH_BYTES = 4096, 65536, 884736
 
 OPS = {"copy": SX_OP_COPY, "scale": SX_OP_SCALE, "add": SX_OP_ADD, "triad": SX_OP_TRIAD,
        "seed": SX_OP_SEED}
@@ -149,6 +150,7 @@ _PROTOS = {
     "sx_batch_completion_ns": [P, C.POINTER(C.c_uint64), SZ],
     "sx_batch_info": [P, C.POINTER(sx_batch_cfg), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
     "sx_batch_destroy": [P],
+    "sx_batch_run_noalloc": [P, C.POINTER(sx_batch_item), SZ, C.POINTER(sx_batch_cfg)],
     "sx_tune": [P, I, I, SZ, C.POINTER(sx_launch_cfg), C.POINTER(C.c_float)],
     "sx_tune_batch": [P, C.POINTER(sx_batch_cfg), C.POINTER(C.c_float)],
     "sx_tune_lookup": [P, I, I, SZ, C.POINTER(sx_launch_cfg)],
@@ -425,6 +427,15 @@ def sx_batch_info(b):
 
 def sx_batch_destroy(b) -> None:
     _check(lib.sx_batch_destroy(b), "sx_batch_destroy")
+
+
+def sx_batch_run_noalloc(stream: int | None, items, cfg=None) -> None:
+    """Run `items` once on `stream` without allocating device memory (see sx.h)."""
+    arr = (sx_batch_item * max(1, len(items)))(*items)
+    c = None
+    if cfg is not None:
+        c = C.byref(cfg if isinstance(cfg, sx_batch_cfg) else sx_batch_cfg(**cfg))
+    _check(lib.sx_batch_run_noalloc(stream, arr, len(items), c), "sx_batch_run_noalloc")
 
 
 def sx_tune(t, op: int, dtype: int, n: int):
