@@ -111,6 +111,13 @@ __device__ __forceinline__ void tile_seed(const DevItem &it, uint64_t start, uin
         o[e] = seeded_value(splitmix_word(it.seed, it.index_base + start + e), lo, span);
 }
 
+// Binary64 construction for lo = -1, hi = 1 on the integer units (see seeded_value_pm1).
+__device__ __forceinline__ void tile_seed_pm1(const DevItem &it, uint64_t start, uint64_t cnt) {
+    double *o = static_cast<double *>(it.out) + start;
+    for (uint64_t e = threadIdx.x; e < cnt; e += blockDim.x)
+        o[e] = seeded_value_pm1(splitmix_word(it.seed, it.index_base + start + e));
+}
+
 template <int VB>
 __device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint64_t cnt) {
     const bool f64 = it.dtype == SX_F64;
@@ -136,7 +143,8 @@ __device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint
             else tile_vector<SX_OP_TRIAD, double, VB, 0>(it, start, cnt);
             break;
         case SX_OP_SEED:
-            if (f64) tile_seed<double>(it, start, cnt);
+            if (f64 && it.q == -1.0 && it.q2 == 1.0) tile_seed_pm1(it, start, cnt);
+            else if (f64) tile_seed<double>(it, start, cnt);
             else tile_seed<float>(it, start, cnt);
             break;
         default: break;

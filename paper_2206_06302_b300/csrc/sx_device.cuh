@@ -196,6 +196,20 @@ __device__ __forceinline__ float seeded_value(uint64_t w, float lo, float span) 
     return __fadd_rn(lo, __fmul_rn(span, u));
 }
 
+// The binary64 value for lo = -1, hi = 1 without the FP64 pipe.  There span = 2, RN(2u) = 2u
+// and RN(-1 + 2u) = k * 2^-52 exactly, with k = (w >> 11) - 2^52 in [-2^52, 2^52), so the
+// double is assembled from k's sign, leading bit and remaining bits (k = 0 gives +0, as
+// -1 + 1 does under round to nearest).  Bit-identical to seeded_value(w, -1.0, 2.0).
+__device__ __forceinline__ double seeded_value_pm1(uint64_t w) {
+    const int64_t k = (int64_t)(w >> 11) - (int64_t)(1ull << 52);
+    if (k == 0) return 0.0;
+    const uint64_t a = k < 0 ? (uint64_t)(-k) : (uint64_t)k;  // 1 .. 2^52
+    const int e = 63 - __clzll((long long)a);                  // 0 .. 52
+    const uint64_t frac = (a << (52 - e)) & 0x000FFFFFFFFFFFFFull;
+    const uint64_t bits = ((uint64_t)(1023 + e - 52) << 52) | frac | (k < 0 ? 0x8000000000000000ull : 0ull);
+    return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

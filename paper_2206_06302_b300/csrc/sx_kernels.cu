@@ -193,10 +193,14 @@ int dispatch_op(const sx_target *t, cudaStream_t s, int op, const void *x, const
 }
 
 // ---- seeded bulk construction ---------------------------------------------------------------
+// PM1: lo = -1, hi = 1, assembled on the integer units (seeded_value_pm1); otherwise the
+// generic formula on the FP64 pipe.
+template <bool PM1>
 __global__ void k_seed_f64(double *out, uint64_t n, uint64_t seed, double lo, double span, uint64_t base) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        out[i] = seeded_value(splitmix_word(seed, base + i), lo, span);
+        const uint64_t w = splitmix_word(seed, base + i);
+        out[i] = PM1 ? seeded_value_pm1(w) : seeded_value(w, lo, span);
     }
 }
 
@@ -216,7 +220,7 @@ __global__ void k_fill(T *out, uint64_t n, T v) {
 
 unsigned setup_blocks(size_t n) {
     uint64_t b = (n + 255) / 256;
-    if (b > 148ull * 16) b = 148ull * 16;
+    if (b > 148ull * 32) b = 148ull * 32;
     return b == 0 ? 1u : (unsigned)b;
 }
 
@@ -381,7 +385,10 @@ int launch_seed(cudaStream_t s, int dtype, void *out, size_t n, uint64_t seed, d
     const unsigned b = setup_blocks(n);
     if (dtype == SX_F64) {
         const double span = hi - lo;
-        k_seed_f64<<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
+        if (lo == -1.0 && hi == 1.0)
+            k_seed_f64<true><<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
+        else
+            k_seed_f64<false><<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
     } else if (dtype == SX_F32) {
         const float lo32 = (float)lo, hi32 = (float)hi;
         const float span = hi32 - lo32;
