@@ -343,11 +343,22 @@ typedef struct sx_server_cfg {
     uint64_t budget_bytes;   /* device arena the server allocates once; admission bound      */
     int32_t mode;            /* SX_SERVE_CONTINUOUS or SX_SERVE_FIFO                          */
     int32_t max_active;      /* requests admitted at once (slots), 1..65536; 0 = 256          */
-    int32_t chunk_bytes;     /* CONTINUOUS: byte budget of one step (1 MiB..2 GiB); 0 = 256 MiB */
-    int32_t steps_in_flight; /* CONTINUOUS: launched steps not yet completed (1..8); 0 = 3    */
+    int32_t chunk_bytes;     /* CONTINUOUS: byte budget of one step (1 MiB..2 GiB); 0 = 128 MiB */
+    int32_t steps_in_flight; /* CONTINUOUS: launched steps not yet completed (1..8); 0 = 4    */
     int32_t threads, blocks_per_sm, vec_bytes;  /* batched-kernel shape; 0 = default        */
     int32_t tile_bytes;      /* CONTINUOUS: work-tile bytes of the batched kernel; 0 = 256 KiB */
+    int32_t policy;          /* CONTINUOUS: how a step's budget is shared, SX_SERVE_POLICY_*  */
+    int32_t serialize_steps; /* CONTINUOUS: 0 = a step may start while the previous one ends
+                                (programmatic dependent launch; pieces that need the previous
+                                step's data wait for it); 1 = steps run strictly one after another */
 } sx_server_cfg;
+
+/* CONTINUOUS sharing policies.  FAIR (default): water-filling; requests with less remaining
+ * work in their phase than an equal share of the step get all of it, the others split the rest
+ * equally.  SHORT_FIRST: requests whose remaining work is at most a quarter of the step budget
+ * go first, shortest first, and finish in the step; the rest of the budget goes to the others
+ * in admission order. */
+enum { SX_SERVE_POLICY_FAIR = 0, SX_SERVE_POLICY_SHORT_FIRST = 1 };
 
 /* Request flags. */
 enum { SX_REQ_AUTO_RELEASE = 1 /* free the arrays as soon as the request is DONE */ };
@@ -384,6 +395,8 @@ typedef struct sx_server_stats {
     uint64_t bytes_moved;     /* STREAM byte count of completed work (seeding included)     */
     uint64_t arena_used, arena_peak, arena_bytes;
     double busy_seconds;      /* host time with at least one step in flight                 */
+    double host_step_seconds;  /* CONTINUOUS: host time spent building and launching steps */
+    double host_admit_seconds; /* host time spent in admission passes                      */
 } sx_server_stats;
 
 /* Start a server thread on the target (its stream carries every launch).  Thread-safe calls:

@@ -315,30 +315,35 @@ uint64_t tile_elems_for(const sx_batch_item &it, int tile_bytes) {
 }
 
 // Fill the device-layout item table and append the item-major tile list.
+// One item in the device layout; returns its tile count.
+uint64_t fill_item(const sx_batch_item &it, int tile_bytes, DevItem &d) {
+    d.op = (uint32_t)it.op;
+    d.dtype = (uint32_t)it.dtype;
+    d.n = it.n;
+    d.x = it.x;
+    d.y = it.y;
+    d.out = it.out;
+    d.q = it.q;
+    d.q2 = it.q2;
+    d.seed = it.seed;
+    d.index_base = it.index_base;
+    d.mulv = item_mul_variant(it);
+    d.pad = 0;
+    const uint64_t te = tile_elems_for(it, tile_bytes);
+    d.tile_elems = (uint32_t)te;
+    const uint64_t nt = (it.n + te - 1) / te;
+    d.ntiles = (uint32_t)std::min<uint64_t>(nt, 0xffffffffull);
+    return nt;
+}
+
 int fill_tables(const sx_batch_item *items, size_t count, int tile_bytes, DevItem *di, DevTile *tiles,
                 size_t tile_cap, size_t *ntiles, uint64_t *bytes) {
     size_t nt_total = 0;
     uint64_t by = 0;
     for (size_t i = 0; i < count; ++i) {
         const auto &it = items[i];
-        DevItem &d = di[i];
-        d.op = (uint32_t)it.op;
-        d.dtype = (uint32_t)it.dtype;
-        d.n = it.n;
-        d.x = it.x;
-        d.y = it.y;
-        d.out = it.out;
-        d.q = it.q;
-        d.q2 = it.q2;
-        d.seed = it.seed;
-        d.index_base = it.index_base;
-        d.mulv = item_mul_variant(it);
-        d.pad = 0;
-        const uint64_t te = tile_elems_for(it, tile_bytes);
-        d.tile_elems = (uint32_t)te;
-        const uint64_t nt = (it.n + te - 1) / te;
+        const uint64_t nt = fill_item(it, tile_bytes, di[i]);
         if (nt > 0xffffffffull) return fail(SX_ERR_INVALID, "item %zu has too many tiles", i);
-        d.ntiles = (uint32_t)nt;
         if (nt_total + nt > tile_cap) return fail(SX_ERR_INVALID, "tile table overflow");
         for (uint64_t k = 0; k < nt; ++k) tiles[nt_total + k] = DevTile{(uint32_t)i, (uint32_t)k};
         nt_total += nt;
@@ -419,25 +424,79 @@ int step_slot_reserve(StepSlot &s, size_t items, size_t tiles) {
     return SX_OK;
 }
 
+// A step's items travel in the launch's own parameter space (up to 32 KB per launch on sm_70+
+// with CUDA 12.1+), so a step costs one launch and no table copies.  Each item's first global
+// tile is in `prefix`; a block finds the item of its tile by binary search over that array.
+constexpr uint32_t kStepMaxItems = 256;
+struct StepParams {
+    uint32_t count, total_tiles;
+    uint32_t prefix[kStepMaxItems + 1];
+    DevItem items[kStepMaxItems];
+};
+static_assert(sizeof(StepParams) <= 32764, "kernel parameter space limit");
+
+// Steps may overlap through programmatic dependent launch: every block allows the next step
+// to launch as soon as it starts (all of a step's blocks are then resident or done, so the next
+// step's blocks only take SM slots this step frees), waits for the previous step before its
+// first tile of an item marked dependent (DevItem.pad bit 0: the operation phase of a request
+// whose inputs were constructed in a step not yet known complete), and waits for it before
+// exiting, so that a step's completion implies its predecessor's.  Without a programmatic
+// predecessor griddepcontrol.wait returns at once.
+template <int VB>
+__global__ void __launch_bounds__(1024) k_batch_step(const __grid_constant__ StepParams p) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    bool waited = false;
+    for (uint32_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
+        uint32_t lo = 0, hi = p.count;  // prefix[lo] <= t < prefix[hi]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (p.prefix[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const DevItem &it = p.items[lo];
+        if ((it.pad & 1u) && !waited) {
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            waited = true;
+        }
+        const uint64_t start = (uint64_t)(t - p.prefix[lo]) * it.tile_elems;
+        const uint64_t cnt = min((uint64_t)it.tile_elems, it.n - start);
+        run_tile<VB>(it, start, cnt);
+    }
+    if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const sx_batch_item *items, size_t count,
-                const sx_batch_cfg &cfg) {
-    const size_t want = count_tiles(items, count, cfg.chunk_bytes);
-    SX_TRY(step_slot_reserve(s, std::max<size_t>(1, count), std::max<size_t>(1, want)));
-    size_t nt = 0;
-    SX_TRY(fill_tables(items, count, cfg.chunk_bytes, static_cast<DevItem *>(s.h_items),
-                       static_cast<DevTile *>(s.h_tiles), s.cap_tiles, &nt, nullptr));
-    if (nt > 0) {
-        SX_CUDA(cudaMemcpyAsync(s.d_items, s.h_items, count * sizeof(DevItem), cudaMemcpyHostToDevice, stream));
-        SX_CUDA(cudaMemcpyAsync(s.d_tiles, s.h_tiles, nt * sizeof(DevTile), cudaMemcpyHostToDevice, stream));
+                const sx_batch_cfg &cfg, const uint8_t *dependent, bool overlap) {
+    SX_TRY(step_slot_reserve(s, 0, 0));  // the completion event
+    static thread_local StepParams p;   // 23 KB: kept off the stack
+    for (size_t first = 0; first < count; first += kStepMaxItems) {
+        const size_t m = std::min<size_t>(kStepMaxItems, count - first);
+        uint32_t tiles = 0;
+        for (size_t i = 0; i < m; ++i) {
+            const uint64_t nti = fill_item(items[first + i], cfg.chunk_bytes, p.items[i]);
+            if ((uint64_t)tiles + nti > 0xffffffffull) return fail(SX_ERR_INVALID, "step has too many tiles");
+            p.items[i].pad = (dependent && dependent[first + i]) ? 1u : 0u;
+            p.prefix[i] = tiles;
+            tiles += (uint32_t)nti;
+        }
+        p.prefix[m] = tiles;
+        p.count = (uint32_t)m;
+        p.total_tiles = tiles;
+        if (tiles == 0) continue;
         uint64_t grid = (uint64_t)t->sm_count * cfg.blocks_per_sm;
-        if (grid > nt) grid = nt;
-        const DevItem *di = static_cast<const DevItem *>(s.d_items);
-        const DevTile *dt = static_cast<const DevTile *>(s.d_tiles);
-        if (cfg.vec_bytes == 16)
-            k_batch<16><<<(unsigned)grid, cfg.threads, 0, stream>>>(di, dt, nt, nullptr, nullptr, nullptr);
-        else
-            k_batch<32><<<(unsigned)grid, cfg.threads, 0, stream>>>(di, dt, nt, nullptr, nullptr, nullptr);
-        SX_CUDA(cudaGetLastError());
+        if (grid > tiles) grid = tiles;
+        cudaLaunchConfig_t lc{};
+        lc.gridDim = dim3((unsigned)grid);
+        lc.blockDim = dim3((unsigned)cfg.threads);
+        lc.dynamicSmemBytes = 0;
+        lc.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = overlap ? 1 : 0;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        if (cfg.vec_bytes == 16) SX_CUDA(cudaLaunchKernelEx(&lc, k_batch_step<16>, p));
+        else SX_CUDA(cudaLaunchKernelEx(&lc, k_batch_step<32>, p));
     }
     SX_CUDA(cudaEventRecord(s.done, stream));
     return SX_OK;

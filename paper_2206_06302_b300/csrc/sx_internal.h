@@ -168,10 +168,12 @@ int step_slot_reserve(StepSlot &s, size_t items, size_t tiles);
 void step_slot_free(StepSlot &s);
 // Number of work tiles `items` are cut into with tiles of `tile_bytes`.
 size_t step_tile_count(const sx_batch_item *items, size_t count, int tile_bytes);
-// Cut `items` into tiles of cfg.chunk_bytes, stage the tables, launch the batched kernel on
-// `stream` and record s.done after it.
+// Launch the batched kernel over `items` (tiles of cfg.chunk_bytes, items passed in the launch's
+// parameters) on `stream` and record s.done after it.  With `overlap` the launch may start while
+// the previous step still runs (programmatic dependent launch); items with dependent[i] != 0 wait
+// for the previous step to complete first.
 int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const sx_batch_item *items,
-                size_t count, const sx_batch_cfg &cfg);
+                size_t count, const sx_batch_cfg &cfg, const uint8_t *dependent, bool overlap);
 
 // ---- autotuner table (sx_tune.cpp) ------------------------------------------------------
 bool tune_table_lookup(const sx_target *t, int op, int dtype, size_t n, sx_launch_cfg *cfg);

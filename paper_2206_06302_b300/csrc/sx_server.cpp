@@ -106,6 +106,8 @@ struct Request {
     int phase = 0;            // 0: construct inputs, 1: operation, 2: all work launched
     uint64_t next = 0;        // next element of the current phase
     int bypassed = 0;         // admission: times a later request was admitted first
+    uint64_t admit_seq = 0;   // order of admission
+    uint64_t inputs_step = 0; // step that holds the last piece of the inputs construction
 };
 
 bool has_y(int op) { return op == SX_OP_ADD || op == SX_OP_TRIAD; }
@@ -118,6 +120,7 @@ size_t phase_bytes_per_elem(const Request &q, int phase) {
 }
 
 struct Step {
+    uint64_t seq = 0;                 // CONTINUOUS: step number, from 1
     int slot = -1;                    // CONTINUOUS: staging slot; FIFO: -1
     cudaEvent_t ev = nullptr;         // FIFO: the request's completion event
     std::vector<Request *> finishing; // requests whose last work is in this step
@@ -150,6 +153,9 @@ struct sx_server {
     std::vector<cudaEvent_t> free_events;
     uint64_t next_id = 1;
     bool stop = false;
+    bool admit_dirty = false;  // arrivals, freed memory or slots since the last admission pass
+    uint64_t step_seq = 0;     // steps launched
+    uint64_t retired_seq = 0;  // every step up to this one is known complete
     int error = SX_OK;
     std::string error_msg;
     sx_server_stats stats{};
@@ -208,6 +214,7 @@ bool try_admit(sx_server *s, Request *q) {
     q->allocated = true;
     q->state = SX_REQ_ACTIVE;
     q->t_admit = now_seconds();
+    q->admit_seq = s->stats.admitted;
     q->phase = 0;
     q->next = 0;
     s->stats.admitted++;
@@ -219,9 +226,13 @@ bool try_admit(sx_server *s, Request *q) {
 // Admission in arrival order; a later request may pass one that does not fit, but a request
 // passed 64 times blocks the queue until it fits (no starvation).
 void admit(sx_server *s) {
+    if (!s->admit_dirty) return;
+    s->admit_dirty = false;
+    const double t0 = now_seconds();
     const size_t slots = (size_t)s->cfg.max_active;
     std::vector<Request *> passed;  // waiting requests a later one may overtake in this pass
-    for (auto it = s->waiting.begin(); it != s->waiting.end();) {
+    size_t tried = 0;
+    for (auto it = s->waiting.begin(); it != s->waiting.end() && tried < 64; ++tried) {
         if (s->active.size() >= slots) break;
         Request *q = *it;
         if (try_admit(s, q)) {
@@ -234,6 +245,8 @@ void admit(sx_server *s) {
         passed.push_back(q);
         ++it;
     }
+    if (!s->waiting.empty() && s->active.size() < slots && tried >= 64) s->admit_dirty = true;
+    s->stats.host_admit_seconds += now_seconds() - t0;
 }
 
 int enqueue_fifo(sx_server *s, Request *q, Step &st) {
@@ -259,31 +272,68 @@ int enqueue_fifo(sx_server *s, Request *q, Step &st) {
 }
 
 // Build and launch one CONTINUOUS step from the active requests' pending work.
+//
+// How the step's byte budget is shared (cfg.policy):
+//   FAIR         water-filling: requests with less remaining work in their phase than an equal
+//                share get all of it; the others split the rest equally.
+//   SHORT_FIRST  requests whose whole remaining work is at most a quarter of the budget go
+//                first, shortest first, and get all of it; the rest of the budget goes to the
+//                others in admission order.
 int launch_step(sx_server *s, bool *launched) {
     *launched = false;
     struct Want {
         Request *q;
-        uint64_t bytes;  // remaining bytes of the current phase
+        uint64_t phase_bytes;  // remaining bytes of the current phase
+        uint64_t total_bytes;  // remaining bytes of the whole request
     };
     std::vector<Want> w;
-    for (Request *q : s->active)
-        if (q->phase < 2) w.push_back({q, (uint64_t)(q->r.n - q->next) * phase_bytes_per_elem(*q, q->phase)});
+    for (Request *q : s->active) {
+        if (q->phase >= 2) continue;
+        const uint64_t pb = (uint64_t)(q->r.n - q->next) * phase_bytes_per_elem(*q, q->phase);
+        const uint64_t later = q->phase == 0 ? (uint64_t)q->r.n * phase_bytes_per_elem(*q, 1) : 0;
+        w.push_back({q, pb, pb + later});
+    }
     if (w.empty()) return SX_OK;
-    std::sort(w.begin(), w.end(), [](const Want &a, const Want &b) { return a.bytes < b.bytes; });
+    const uint64_t step_budget = (uint64_t)(uint32_t)s->cfg.chunk_bytes;
+    std::vector<uint64_t> grant(w.size(), 0);  // elements of the current phase this step
+    auto whole_units = [](uint64_t elems) { return std::max<uint64_t>(elems / 64 * 64, 64); };
+    if (s->cfg.policy == SX_SERVE_POLICY_FAIR) {
+        std::sort(w.begin(), w.end(), [](const Want &a, const Want &b) { return a.phase_bytes < b.phase_bytes; });
+        uint64_t budget = step_budget;
+        for (size_t i = 0; i < w.size(); ++i) {
+            const uint64_t per = phase_bytes_per_elem(*w[i].q, w[i].q->phase);
+            const uint64_t remaining = w[i].q->r.n - w[i].q->next;
+            grant[i] = std::min(remaining, whole_units(budget / (w.size() - i) / per));
+            budget -= std::min(budget, grant[i] * per);
+        }
+    } else {
+        const uint64_t short_bytes = step_budget / 4;
+        std::sort(w.begin(), w.end(), [short_bytes](const Want &a, const Want &b) {
+            const bool sa = a.total_bytes <= short_bytes, sb = b.total_bytes <= short_bytes;
+            if (sa != sb) return sa;
+            if (sa) return a.total_bytes < b.total_bytes;
+            return a.q->admit_seq < b.q->admit_seq;
+        });
+        uint64_t budget = step_budget;
+        for (size_t i = 0; i < w.size() && budget > 0; ++i) {
+            const uint64_t per = phase_bytes_per_elem(*w[i].q, w[i].q->phase);
+            const uint64_t remaining = w[i].q->r.n - w[i].q->next;
+            grant[i] = std::min(remaining, whole_units(budget / per));
+            budget -= std::min(budget, grant[i] * per);
+        }
+    }
     const int slot = s->free_slots.back();
     s->free_slots.pop_back();
     std::vector<sx_batch_item> items;
+    std::vector<uint8_t> dep;  // operation pieces whose inputs come from a step still in flight
     Step st;
     st.slot = slot;
-    uint64_t budget = (uint64_t)(uint32_t)s->cfg.chunk_bytes;
+    st.seq = s->step_seq + 1;
     for (size_t i = 0; i < w.size(); ++i) {
+        if (grant[i] == 0) continue;
         Request *q = w[i].q;
-        const uint64_t share = budget / (w.size() - i);
         const uint64_t per = phase_bytes_per_elem(*q, q->phase);
-        uint64_t elems = share / per;
-        elems = std::max<uint64_t>(elems / 64 * 64, 64);  // whole 64-element units, at least one
-        const uint64_t remaining = q->r.n - q->next;
-        if (elems >= remaining) elems = remaining;
+        const uint64_t elems = grant[i];
         const uint64_t lo = q->next, hi = lo + elems;
         const sx_request &r = q->r;
         const size_t es = dtype_size(r.dtype);
@@ -298,10 +348,12 @@ int launch_step(sx_server *s, bool *launched) {
             it.seed = r.seed_x;
             it.index_base = lo;
             items.push_back(it);
+            dep.push_back(0);
             if (has_y(r.op)) {
                 it.out = (char *)ptr_of(s, q, 1) + lo * es;
                 it.seed = r.seed_y;
                 items.push_back(it);
+                dep.push_back(0);
             }
         } else {
             sx_batch_item it{};
@@ -313,22 +365,37 @@ int launch_step(sx_server *s, bool *launched) {
             it.out = (char *)ptr_of(s, q, 2) + lo * es;
             it.q = r.q;
             items.push_back(it);
+            dep.push_back(q->inputs_step > s->retired_seq ? 1 : 0);
         }
         st.bytes += elems * per;
-        budget -= std::min(budget, elems * per);
         q->next = hi;
         if (q->next == r.n) {
             q->next = 0;
+            if (q->phase == 0) q->inputs_step = st.seq;
             q->phase++;
             if (q->phase == 2) st.finishing.push_back(q);
         }
     }
-    const int rc = step_launch(s->t, s->t->stream, s->slots[slot], items.data(), items.size(), s->kcfg);
+    // independent pieces first, so that blocks reach the ones that must wait as late as possible
+    std::vector<size_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&dep](size_t a, size_t b) { return dep[a] < dep[b]; });
+    std::vector<sx_batch_item> sorted(items.size());
+    std::vector<uint8_t> sdep(items.size());
+    for (size_t i = 0; i < order.size(); ++i) {
+        sorted[i] = items[order[i]];
+        sdep[i] = dep[order[i]];
+    }
+    items.swap(sorted);
+    dep.swap(sdep);
+    const int rc = step_launch(s->t, s->t->stream, s->slots[slot], items.data(), items.size(), s->kcfg,
+                               dep.data(), s->cfg.serialize_steps == 0);
     if (rc != SX_OK) {
         s->free_slots.push_back(slot);
         return rc;
     }
     st.t_launch = now_seconds();
+    s->step_seq = st.seq;
     s->inflight.push_back(std::move(st));
     s->stats.steps++;
     s->stats.launches++;
@@ -355,8 +422,10 @@ bool retire(sx_server *s) {
             s->stats.completed++;
             s->active.erase(std::find(s->active.begin(), s->active.end(), q));
             if (q->r.flags & SX_REQ_AUTO_RELEASE) release_arrays(s, q);
+            s->admit_dirty = true;
         }
         s->stats.bytes_moved += st.bytes;
+        if (st.slot >= 0) s->retired_seq = st.seq;
         if (st.slot >= 0) s->free_slots.push_back(st.slot);
         else s->free_events.push_back(st.ev);
         s->inflight.pop_front();
@@ -388,7 +457,9 @@ void server_loop(sx_server *s) {
                     launched = true;
                 }
             } else if (!s->free_slots.empty()) {
+                const double tl = now_seconds();
                 rc = launch_step(s, &launched);
+                s->stats.host_step_seconds += now_seconds() - tl;
             }
             if (rc != SX_OK) {
                 s->error = rc;
@@ -464,6 +535,7 @@ void submit_locked(sx_server *s, const sx_request &r, uint64_t id, double t) {
         return;
     }
     s->waiting.push_back(raw);
+    s->admit_dirty = true;
 }
 
 Request *find(sx_server *s, uint64_t id) {
@@ -483,8 +555,12 @@ int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out) {
     if (c.mode != SX_SERVE_CONTINUOUS && c.mode != SX_SERVE_FIFO) return fail(SX_ERR_INVALID, "mode %d", c.mode);
     if (c.budget_bytes == 0) return fail(SX_ERR_INVALID, "budget_bytes must be positive");
     if (c.max_active == 0) c.max_active = 256;
-    if (c.chunk_bytes == 0) c.chunk_bytes = 256 << 20;
-    if (c.steps_in_flight == 0) c.steps_in_flight = 3;
+    if (c.chunk_bytes == 0) c.chunk_bytes = 128 << 20;
+    if (c.steps_in_flight == 0) c.steps_in_flight = 4;
+    if (c.policy != SX_SERVE_POLICY_SHORT_FIRST && c.policy != SX_SERVE_POLICY_FAIR)
+        return fail(SX_ERR_INVALID, "policy %d", c.policy);
+    if (c.serialize_steps != 0 && c.serialize_steps != 1)
+        return fail(SX_ERR_INVALID, "serialize_steps %d: 0 or 1", c.serialize_steps);
     if (c.max_active < 1 || c.max_active > 65536) return fail(SX_ERR_INVALID, "max_active %d", c.max_active);
     if (c.chunk_bytes < (1 << 20)) return fail(SX_ERR_INVALID, "chunk_bytes %d below 1 MiB", c.chunk_bytes);
     if (c.steps_in_flight < 1 || c.steps_in_flight > 8) return fail(SX_ERR_INVALID, "steps_in_flight %d", c.steps_in_flight);
@@ -652,6 +728,7 @@ int sx_server_release(sx_server *s, uint64_t id) {
         if (q->state != SX_REQ_DONE && q->state != SX_REQ_REJECTED)
             return fail(SX_ERR_STATE, "request %llu is not finished", (unsigned long long)id);
         release_arrays(s, q);
+        s->admit_dirty = true;
         if (q->state == SX_REQ_DONE) q->state = SX_REQ_RELEASED;
     }
     s->cv.notify_one();  // memory freed: admission may proceed

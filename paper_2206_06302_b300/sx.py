@@ -27,6 +27,7 @@ SX_PAR, SX_PAR_TASK = 1, 2
 SX_VARIANT_AUTO, SX_VARIANT_VECTOR, SX_VARIANT_BULK = 0, 1, 2
 SX_FN_TO_UPPER, SX_FN_TO_LOWER = 1, 2
 SX_SERVE_CONTINUOUS, SX_SERVE_FIFO = 0, 1
+SX_SERVE_POLICY_FAIR, SX_SERVE_POLICY_SHORT_FIRST = 0, 1
 SX_REQ_QUEUED, SX_REQ_ACTIVE, SX_REQ_DONE, SX_REQ_REJECTED, SX_REQ_RELEASED = 0, 1, 2, 3, 4
 SX_REQ_AUTO_RELEASE = 1
 SX_NOALLOC_MAX_ITEMS, SX_NOALLOC_MAX_TILES, SX_NOALLOC_SCRATCH_BYTES = 4096, 65536, 884736
@@ -78,7 +79,7 @@ class sx_server_cfg(C.Structure):
     _fields_ = [("budget_bytes", C.c_uint64), ("mode", C.c_int32), ("max_active", C.c_int32),
                 ("chunk_bytes", C.c_int32), ("steps_in_flight", C.c_int32),
                 ("threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("vec_bytes", C.c_int32),
-                ("tile_bytes", C.c_int32)]
+                ("tile_bytes", C.c_int32), ("policy", C.c_int32), ("serialize_steps", C.c_int32)]
 
 
 class sx_request(C.Structure):
@@ -96,7 +97,8 @@ class sx_request_status(C.Structure):
 class sx_server_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("submitted", "admitted", "completed", "rejected",
                                           "steps", "launches", "bytes_moved", "arena_used",
-                                          "arena_peak", "arena_bytes")] + [("busy_seconds", C.c_double)]
+                                          "arena_peak", "arena_bytes")] + [(n, C.c_double) for n in (
+                                              "busy_seconds", "host_step_seconds", "host_admit_seconds")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -140,3 +140,17 @@ def test_bad_calls(target):
     with pytest.raises(sx.SxError) as ei:
         sx.sx_server_wait(s, 999, 10)
     sx.sx_server_destroy(s)
+
+
+@pytest.mark.parametrize("policy", [sx.SX_SERVE_POLICY_SHORT_FIRST, sx.SX_SERVE_POLICY_FAIR])
+@pytest.mark.parametrize("serialize", [0, 1])
+def test_policies_and_step_overlap(target, policy, serialize):
+    """Both sharing policies, with consecutive steps overlapping (operation pieces whose inputs
+    were built in a step still running wait for it) and strictly serialized."""
+    reqs = _requests(160, seed=6, lo_exp=6, hi_exp=20)
+    s = sx.sx_server_create(target, budget_bytes=512 << 20, chunk_bytes=2 << 20, tile_bytes=16384,
+                            steps_in_flight=4, policy=policy, serialize_steps=serialize)
+    ids = [sx.sx_server_submit(s, **r) for r in reqs]
+    _check_all(s, ids, reqs, f"policy {policy} serialize {serialize}")
+    assert sx.sx_server_stats_get(s)["steps"] > 10
+    sx.sx_server_destroy(s)
