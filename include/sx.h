@@ -340,11 +340,13 @@ typedef struct sx_server sx_server;
  * the stream, in arrival order. */
 enum { SX_SERVE_CONTINUOUS = 0, SX_SERVE_FIFO = 1 };
 typedef struct sx_server_cfg {
-    uint64_t budget_bytes;   /* device arena the server allocates once; admission bound      */
+    uint64_t budget_bytes;   /* device arena the server allocates once; admission bound.  Large
+                                requests (more than 1/16 of the arena) hold memory at most four
+                                at a time, so the rest stays open to smaller ones             */
     int32_t mode;            /* SX_SERVE_CONTINUOUS or SX_SERVE_FIFO                          */
     int32_t max_active;      /* requests admitted at once (slots), 1..65536; 0 = 256          */
-    int32_t chunk_bytes;     /* CONTINUOUS: byte budget of one step (1 MiB..2 GiB); 0 = 128 MiB */
-    int32_t steps_in_flight; /* CONTINUOUS: launched steps not yet completed (1..8); 0 = 4    */
+    int32_t chunk_bytes;     /* CONTINUOUS: byte budget of one step (1 MiB..2 GiB); 0 = 512 MiB */
+    int32_t steps_in_flight; /* CONTINUOUS: launched steps not yet completed (1..8); 0 = 2    */
     int32_t threads, blocks_per_sm, vec_bytes;  /* batched-kernel shape; 0 = default        */
     int32_t tile_bytes;      /* CONTINUOUS: work-tile bytes of the batched kernel; 0 = 256 KiB */
     int32_t policy;          /* CONTINUOUS: how a step's budget is shared, SX_SERVE_POLICY_*  */
@@ -353,12 +355,14 @@ typedef struct sx_server_cfg {
                                 step's data wait for it); 1 = steps run strictly one after another */
 } sx_server_cfg;
 
-/* CONTINUOUS sharing policies.  FAIR (default): water-filling; requests with less remaining
- * work in their phase than an equal share of the step get all of it, the others split the rest
- * equally.  SHORT_FIRST: requests whose remaining work is at most a quarter of the step budget
- * go first, shortest first, and finish in the step; the rest of the budget goes to the others
- * in admission order. */
-enum { SX_SERVE_POLICY_FAIR = 0, SX_SERVE_POLICY_SHORT_FIRST = 1 };
+/* CONTINUOUS sharing policies.  SRPT (default): shortest remaining work first; each request in
+ * that order gets all of its current phase's remaining work until the step budget is spent (it
+ * keeps the fewest requests, and so the least arena memory, in the system).  FAIR: water-filling;
+ * requests with less remaining work in their phase than an equal share of the step get all of
+ * it, the others split the rest equally.  SHORT_FIRST: requests whose remaining work is at most
+ * a quarter of the step budget go first, shortest first; the rest of the budget goes to the
+ * others in admission order. */
+enum { SX_SERVE_POLICY_SRPT = 0, SX_SERVE_POLICY_FAIR = 1, SX_SERVE_POLICY_SHORT_FIRST = 2 };
 
 /* Request flags. */
 enum { SX_REQ_AUTO_RELEASE = 1 /* free the arrays as soon as the request is DONE */ };

@@ -8,13 +8,15 @@
 // than the whole arena are rejected at submission.
 //
 // CONTINUOUS mode batches requests continuously.  A step is one launch of the batched kernel
-// (sx_batch.cu) over a list of pieces: for every active request a range of its current phase
-// (phase 0 constructs x and y, phase 1 runs the operation; a request never has both phases in
-// one step, so stream order keeps the phases in order).  The step's byte budget is shared out by
-// water-filling: requests with less remaining work than the fair share finish in this step, the
-// rest split what is left.  Up to steps_in_flight steps are queued on the stream; the thread
-// builds the next step while the GPU runs the previous ones, admits new arrivals between
-// steps, and marks a request DONE when the step holding its last piece has completed.
+// (sx_batch.cu) over a list of pieces, passed in the launch's parameters: for active requests a
+// range of their current phase (phase 0 constructs x and y, phase 1 runs the operation; a request
+// never has both phases in one step).  The step's byte budget goes by policy, shortest remaining
+// work first by default, so short requests finish in a step or two while long ones advance in
+// the rest.  Up to steps_in_flight steps are queued on the stream and consecutive steps overlap
+// through programmatic dependent launch; a piece that needs the inputs built in a step not yet
+// known complete waits for it on the device.  The thread builds the next step while the GPU runs
+// the previous ones, admits arrivals between steps, and marks a request DONE when the step
+// holding its last piece has completed.
 //
 // FIFO mode is the per-call baseline: each admitted request is enqueued at once as its own
 // launches (construct x, construct y, operation) in arrival order, like a client calling the
@@ -24,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -154,8 +157,15 @@ struct sx_server {
     uint64_t next_id = 1;
     bool stop = false;
     bool admit_dirty = false;  // arrivals, freed memory or slots since the last admission pass
+    // threads (other than the server's) waiting for or holding the lock: the server thread
+    // neither spins nor polls the GPU with the lock held while this is non-zero
+    std::atomic<int> contenders{0};
+    // bumped on every arrival and every release of arena memory: the server thread watches it
+    // without the lock to know that admission has something to do
+    std::atomic<uint64_t> arrivals{0};
     uint64_t step_seq = 0;     // steps launched
     uint64_t retired_seq = 0;  // every step up to this one is known complete
+    int large_held = 0;        // large requests holding arena memory (see kMaxLarge)
     int error = SX_OK;
     std::string error_msg;
     sx_server_stats stats{};
@@ -168,8 +178,19 @@ struct sx_server {
 namespace sx {
 namespace {
 
+// Large requests hold more than 1/16 of the arena.  At most kMaxLarge of them hold memory at a
+// time, so the rest of the arena stays open to smaller requests: under fair sharing a long
+// request keeps its memory for long, and without the cap a handful of them could fill the
+// arena and stall every admission behind them.
+constexpr int kMaxLarge = 4;
+
+bool is_large(const sx_server *s, const Request *q) {
+    return (q->bytes[0] + q->bytes[1] + q->bytes[2]) * 16 > s->arena->size();
+}
+
 void release_arrays(sx_server *s, Request *q) {
     if (!q->allocated) return;
+    if (is_large(s, q)) s->large_held--;
     for (int k = 0; k < 3; ++k)
         if (q->bytes[k]) s->arena->release(q->off[k], q->bytes[k]);
     q->allocated = false;
@@ -196,6 +217,8 @@ size_t rounded_total(const size_t bytes[3]) {
 bool try_admit(sx_server *s, Request *q) {
     size_t bytes[3];
     request_sizes(q->r, bytes);
+    const bool large = (bytes[0] + bytes[1] + bytes[2]) * 16 > s->arena->size();
+    if (large && s->large_held >= kMaxLarge) return false;
     size_t off[3] = {0, 0, 0};
     int k = 0;
     for (; k < 3; ++k) {
@@ -212,6 +235,7 @@ bool try_admit(sx_server *s, Request *q) {
         q->bytes[j] = bytes[j];
     }
     q->allocated = true;
+    if (large) s->large_held++;
     q->state = SX_REQ_ACTIVE;
     q->t_admit = now_seconds();
     q->admit_seq = s->stats.admitted;
@@ -274,6 +298,8 @@ int enqueue_fifo(sx_server *s, Request *q, Step &st) {
 // Build and launch one CONTINUOUS step from the active requests' pending work.
 //
 // How the step's byte budget is shared (cfg.policy):
+//   SRPT         shortest remaining work first: in that order each request gets all of its
+//                current phase's remaining work until the budget is spent.
 //   FAIR         water-filling: requests with less remaining work in their phase than an equal
 //                share get all of it; the others split the rest equally.
 //   SHORT_FIRST  requests whose whole remaining work is at most a quarter of the budget go
@@ -307,13 +333,20 @@ int launch_step(sx_server *s, bool *launched) {
             budget -= std::min(budget, grant[i] * per);
         }
     } else {
-        const uint64_t short_bytes = step_budget / 4;
-        std::sort(w.begin(), w.end(), [short_bytes](const Want &a, const Want &b) {
-            const bool sa = a.total_bytes <= short_bytes, sb = b.total_bytes <= short_bytes;
-            if (sa != sb) return sa;
-            if (sa) return a.total_bytes < b.total_bytes;
-            return a.q->admit_seq < b.q->admit_seq;
-        });
+        if (s->cfg.policy == SX_SERVE_POLICY_SRPT) {
+            std::sort(w.begin(), w.end(), [](const Want &a, const Want &b) {
+                if (a.total_bytes != b.total_bytes) return a.total_bytes < b.total_bytes;
+                return a.q->admit_seq < b.q->admit_seq;
+            });
+        } else {
+            const uint64_t short_bytes = step_budget / 4;
+            std::sort(w.begin(), w.end(), [short_bytes](const Want &a, const Want &b) {
+                const bool sa = a.total_bytes <= short_bytes, sb = b.total_bytes <= short_bytes;
+                if (sa != sb) return sa;
+                if (sa) return a.total_bytes < b.total_bytes;
+                return a.q->admit_seq < b.q->admit_seq;
+            });
+        }
         uint64_t budget = step_budget;
         for (size_t i = 0; i < w.size() && budget > 0; ++i) {
             const uint64_t per = phase_bytes_per_elem(*w[i].q, w[i].q->phase);
@@ -476,14 +509,46 @@ void server_loop(sx_server *s) {
         const bool work_pending = !s->active.empty() || !s->inflight.empty();
         if (s->stop && !work_pending) break;
         if (s->stop && s->error != SX_OK && s->inflight.empty()) break;
-        if (launched || retired) continue;
-        if (!s->inflight.empty()) {
-            // GPU busy: poll its completion without holding the lock
+        // Between passes the lock goes to any thread that asked for it: the server thread does
+        // not take it back while one is announced (an unlock followed at once by a lock would
+        // win the race against the woken thread every time and starve submitters).
+        auto wait_contenders = [s]() {  // at most 100 us, so callers polling in a loop cannot starve it
+            const double until = now_seconds() + 1e-4;
+            while (s->contenders.load(std::memory_order_acquire) && now_seconds() < until)
+                std::this_thread::yield();
+        };
+        auto let_others_in = [s, &lk, &wait_contenders]() {
+            if (!s->contenders.load(std::memory_order_acquire)) return;
             lk.unlock();
-            std::this_thread::yield();
+            wait_contenders();
+            lk.lock();
+        };
+        if (launched || retired) {
+            let_others_in();
+            continue;
+        }
+        const uint64_t seen = s->arrivals.load(std::memory_order_acquire);
+        if (!s->inflight.empty()) {
+            // GPU busy: wait for the oldest step without the lock; come back early for arrivals
+            // or freed memory (admission), and let callers that want the lock have it
+            Step &front = s->inflight.front();
+            cudaEvent_t ev = front.slot >= 0 ? s->slots[front.slot].done : front.ev;
+            lk.unlock();
+            while (cudaEventQuery(ev) == cudaErrorNotReady &&
+                   s->arrivals.load(std::memory_order_acquire) == seen)
+                std::this_thread::yield();
+            wait_contenders();
             lk.lock();
         } else {
-            s->cv.wait_for(lk, std::chrono::milliseconds(5));
+            // idle: watch for arrivals for a short while without the lock, then sleep
+            lk.unlock();
+            const double until = now_seconds() + 2e-4;
+            while (s->arrivals.load(std::memory_order_acquire) == seen && now_seconds() < until)
+                std::this_thread::yield();
+            wait_contenders();
+            lk.lock();
+            if (s->arrivals.load(std::memory_order_acquire) == seen && !s->stop)
+                s->cv.wait_for(lk, std::chrono::milliseconds(5));
         }
     }
     // reject what never got in
@@ -494,6 +559,20 @@ void server_loop(sx_server *s) {
     s->waiting.clear();
     s->done_cv.notify_all();
 }
+
+// The lock as taken by API calls: announced first, so the server thread lets go of it.
+struct ApiLock {
+    sx_server *s;
+    std::unique_lock<std::mutex> lk;
+    explicit ApiLock(sx_server *sv) : s(sv) {
+        s->contenders.fetch_add(1, std::memory_order_relaxed);
+        lk = std::unique_lock<std::mutex>(s->mu);
+    }
+    ~ApiLock() {
+        if (lk.owns_lock()) lk.unlock();
+        s->contenders.fetch_sub(1, std::memory_order_relaxed);
+    }
+};
 
 void fill_status(sx_server *s, const Request *q, sx_request_status *st) {
     st->state = q->state;
@@ -536,6 +615,7 @@ void submit_locked(sx_server *s, const sx_request &r, uint64_t id, double t) {
     }
     s->waiting.push_back(raw);
     s->admit_dirty = true;
+    s->arrivals.fetch_add(1, std::memory_order_release);
 }
 
 Request *find(sx_server *s, uint64_t id) {
@@ -555,9 +635,10 @@ int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out) {
     if (c.mode != SX_SERVE_CONTINUOUS && c.mode != SX_SERVE_FIFO) return fail(SX_ERR_INVALID, "mode %d", c.mode);
     if (c.budget_bytes == 0) return fail(SX_ERR_INVALID, "budget_bytes must be positive");
     if (c.max_active == 0) c.max_active = 256;
-    if (c.chunk_bytes == 0) c.chunk_bytes = 128 << 20;
-    if (c.steps_in_flight == 0) c.steps_in_flight = 4;
-    if (c.policy != SX_SERVE_POLICY_SHORT_FIRST && c.policy != SX_SERVE_POLICY_FAIR)
+    if (c.chunk_bytes == 0) c.chunk_bytes = 512 << 20;
+    if (c.steps_in_flight == 0) c.steps_in_flight = 2;
+    if (c.policy != SX_SERVE_POLICY_SHORT_FIRST && c.policy != SX_SERVE_POLICY_FAIR &&
+        c.policy != SX_SERVE_POLICY_SRPT)
         return fail(SX_ERR_INVALID, "policy %d", c.policy);
     if (c.serialize_steps != 0 && c.serialize_steps != 1)
         return fail(SX_ERR_INVALID, "serialize_steps %d: 0 or 1", c.serialize_steps);
@@ -613,9 +694,9 @@ int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out) {
 int sx_server_submit(sx_server *s, const sx_request *r, uint64_t *id) {
     if (!s || !id) return fail(SX_ERR_INVALID, "NULL argument");
     SX_TRY(check_request(r));
-    const double t = now_seconds();
+    const double t = now_seconds();  // the arrival, before any wait for the lock
     {
-        std::lock_guard<std::mutex> g(s->mu);
+        ApiLock g(s);
         if (s->stop) return fail(SX_ERR_STATE, "server is stopping");
         *id = s->next_id++;
         submit_locked(s, *r, *id, t);
@@ -633,7 +714,7 @@ int sx_server_replay(sx_server *s, const sx_request *reqs, const double *t_arriv
     }
     uint64_t first;
     {
-        std::lock_guard<std::mutex> g(s->mu);
+        ApiLock g(s);
         if (s->stop) return fail(SX_ERR_STATE, "server is stopping");
         first = s->next_id;
         s->next_id += count;
@@ -642,7 +723,7 @@ int sx_server_replay(sx_server *s, const sx_request *reqs, const double *t_arriv
     std::vector<sx_request> rs(reqs, reqs + count);
     std::vector<double> ts(t_arrival, t_arrival + count);
     const double t0 = now_seconds();
-    std::lock_guard<std::mutex> g(s->mu);
+    ApiLock g(s);
     s->replayers.emplace_back([s, rs = std::move(rs), ts = std::move(ts), first, t0]() {
         for (size_t k = 0; k < rs.size(); ++k) {
             const double due = t0 + ts[k];
@@ -655,8 +736,9 @@ int sx_server_replay(sx_server *s, const sx_request *reqs, const double *t_arriv
                     std::this_thread::yield();
             }
             {
-                std::lock_guard<std::mutex> g2(s->mu);
-                submit_locked(s, rs[k], first + k, now_seconds());
+                // the scheduled arrival time is the request's arrival, whatever the wait after it
+                ApiLock g2(s);
+                submit_locked(s, rs[k], first + k, due);
             }
             s->cv.notify_one();
         }
@@ -666,7 +748,7 @@ int sx_server_replay(sx_server *s, const sx_request *reqs, const double *t_arriv
 
 int sx_server_poll(sx_server *s, uint64_t id, sx_request_status *st) {
     if (!s || !st) return fail(SX_ERR_INVALID, "NULL argument");
-    std::lock_guard<std::mutex> g(s->mu);
+    ApiLock g(s);
     Request *q = find(s, id);
     if (!q) return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
     fill_status(s, q, st);
@@ -675,7 +757,8 @@ int sx_server_poll(sx_server *s, uint64_t id, sx_request_status *st) {
 
 int sx_server_wait(sx_server *s, uint64_t id, int64_t timeout_ms, sx_request_status *st) {
     if (!s) return fail(SX_ERR_INVALID, "NULL argument");
-    std::unique_lock<std::mutex> lk(s->mu);
+    ApiLock al(s);
+    std::unique_lock<std::mutex> &lk = al.lk;
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
     for (;;) {
         Request *q = find(s, id);
@@ -688,12 +771,16 @@ int sx_server_wait(sx_server *s, uint64_t id, int64_t timeout_ms, sx_request_sta
         }
         if (s->error != SX_OK) return fail(s->error, "server failed: %s", s->error_msg.c_str());
         if (timeout_ms < 0) {
+            s->contenders.fetch_sub(1, std::memory_order_relaxed);  // asleep, not contending
             s->done_cv.wait_for(lk, std::chrono::milliseconds(50));
+            s->contenders.fetch_add(1, std::memory_order_relaxed);
         } else {
             if (std::chrono::steady_clock::now() >= deadline)
                 return fail(SX_ERR_TIMEOUT, "request %llu not done after %lld ms", (unsigned long long)id,
                             (long long)timeout_ms);
+            s->contenders.fetch_sub(1, std::memory_order_relaxed);
             s->done_cv.wait_until(lk, std::min(deadline, std::chrono::steady_clock::now() + std::chrono::milliseconds(50)));
+            s->contenders.fetch_add(1, std::memory_order_relaxed);
         }
     }
 }
@@ -704,7 +791,7 @@ int sx_server_read(sx_server *s, uint64_t id, int which, void *host, size_t n) {
     const void *src;
     size_t bytes;
     {
-        std::lock_guard<std::mutex> g(s->mu);
+        ApiLock g(s);
         Request *q = find(s, id);
         if (!q) return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
         if (q->state != SX_REQ_DONE || !q->allocated) return fail(SX_ERR_STATE, "request %llu has no resident result", (unsigned long long)id);
@@ -722,13 +809,14 @@ int sx_server_read(sx_server *s, uint64_t id, int which, void *host, size_t n) {
 int sx_server_release(sx_server *s, uint64_t id) {
     if (!s) return fail(SX_ERR_INVALID, "NULL argument");
     {
-        std::lock_guard<std::mutex> g(s->mu);
+        ApiLock g(s);
         Request *q = find(s, id);
         if (!q) return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
         if (q->state != SX_REQ_DONE && q->state != SX_REQ_REJECTED)
             return fail(SX_ERR_STATE, "request %llu is not finished", (unsigned long long)id);
         release_arrays(s, q);
         s->admit_dirty = true;
+        s->arrivals.fetch_add(1, std::memory_order_release);
         if (q->state == SX_REQ_DONE) q->state = SX_REQ_RELEASED;
     }
     s->cv.notify_one();  // memory freed: admission may proceed
@@ -737,7 +825,7 @@ int sx_server_release(sx_server *s, uint64_t id) {
 
 int sx_server_stats_get(sx_server *s, sx_server_stats *st) {
     if (!s || !st) return fail(SX_ERR_INVALID, "NULL argument");
-    std::lock_guard<std::mutex> g(s->mu);
+    ApiLock g(s);
     *st = s->stats;
     st->arena_used = s->arena->used();
     st->arena_peak = s->arena->peak();
@@ -749,13 +837,14 @@ int sx_server_destroy(sx_server *s) {
     if (!s) return fail(SX_ERR_INVALID, "NULL argument");
     std::vector<std::thread> reps;
     {
-        std::lock_guard<std::mutex> g(s->mu);
+        ApiLock g(s);
         reps.swap(s->replayers);
     }
     for (auto &r : reps) r.join();  // every replayed request is submitted
     {
-        std::lock_guard<std::mutex> g(s->mu);
+        ApiLock g(s);
         s->stop = true;
+        s->arrivals.fetch_add(1, std::memory_order_release);
     }
     s->cv.notify_all();
     if (s->th.joinable()) s->th.join();

@@ -27,7 +27,7 @@ SX_PAR, SX_PAR_TASK = 1, 2
 SX_VARIANT_AUTO, SX_VARIANT_VECTOR, SX_VARIANT_BULK = 0, 1, 2
 SX_FN_TO_UPPER, SX_FN_TO_LOWER = 1, 2
 SX_SERVE_CONTINUOUS, SX_SERVE_FIFO = 0, 1
-SX_SERVE_POLICY_FAIR, SX_SERVE_POLICY_SHORT_FIRST = 0, 1
+SX_SERVE_POLICY_SRPT, SX_SERVE_POLICY_FAIR, SX_SERVE_POLICY_SHORT_FIRST = 0, 1, 2
 SX_REQ_QUEUED, SX_REQ_ACTIVE, SX_REQ_DONE, SX_REQ_REJECTED, SX_REQ_RELEASED = 0, 1, 2, 3, 4
 SX_REQ_AUTO_RELEASE = 1
 SX_NOALLOC_MAX_ITEMS, SX_NOALLOC_MAX_TILES, SX_NOALLOC_SCRATCH_BYTES = 4096, 65536, 884736

@@ -110,21 +110,22 @@ def test_admission_waits_for_memory_and_rejects_oversize(target):
 
 
 def test_short_requests_overtake_a_long_one(target):
-    """Continuous batching: short requests submitted while a long one runs finish before it;
-    with the per-call FIFO they finish after it."""
+    """Continuous batching: short requests that arrive while a long one runs finish before it;
+    with the per-call FIFO they finish after it.  Arrivals are replayed by the library."""
+    long_req = sx.sx_request(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=1 << 28, q=3.0, seed_x=1,
+                             seed_y=2, lo=-1.0, hi=1.0, flags=sx.SX_REQ_AUTO_RELEASE)
+    short_req = sx.sx_request(op=sx.SX_OP_ADD, dtype=sx.SX_F32, n=1 << 12, q=3.0, seed_x=3,
+                              seed_y=4, lo=-1.0, hi=1.0, flags=sx.SX_REQ_AUTO_RELEASE)
+    times = [0.0] + [2e-4 + 5e-5 * k for k in range(8)]  # shorts while the long one runs
     order = {}
     for mode in (sx.SX_SERVE_CONTINUOUS, sx.SX_SERVE_FIFO):
         s = sx.sx_server_create(target, budget_bytes=8 << 30, mode=mode, chunk_bytes=64 << 20)
-        long_id = sx.sx_server_submit(s, op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=1 << 28, q=3.0,
-                                      flags=sx.SX_REQ_AUTO_RELEASE)
-        short = [sx.sx_server_submit(s, op=sx.SX_OP_ADD, dtype=sx.SX_F32, n=1 << 12,
-                                     flags=sx.SX_REQ_AUTO_RELEASE) for _ in range(8)]
-        t_long = sx.sx_server_wait(s, long_id, 60000)["t_done"]
-        t_short = [sx.sx_server_wait(s, r, 60000)["t_done"] for r in short]
-        order[mode] = sum(t < t_long for t in t_short)
+        ids = sx.sx_server_replay(s, [long_req] + [short_req] * 8, times)
+        done = [sx.sx_server_wait(s, r, 60000)["t_done"] for r in ids]
+        order[mode] = (sum(t < done[0] for t in done[1:]), [round((t - done[0]) * 1e3, 3) for t in done[1:]])
         sx.sx_server_destroy(s)
-    assert order[sx.SX_SERVE_CONTINUOUS] == 8
-    assert order[sx.SX_SERVE_FIFO] == 0
+    assert order[sx.SX_SERVE_CONTINUOUS][0] == 8, order
+    assert order[sx.SX_SERVE_FIFO][0] == 0, order
 
 
 def test_bad_calls(target):
@@ -142,7 +143,8 @@ def test_bad_calls(target):
     sx.sx_server_destroy(s)
 
 
-@pytest.mark.parametrize("policy", [sx.SX_SERVE_POLICY_SHORT_FIRST, sx.SX_SERVE_POLICY_FAIR])
+@pytest.mark.parametrize("policy", [sx.SX_SERVE_POLICY_SRPT, sx.SX_SERVE_POLICY_FAIR,
+                                    sx.SX_SERVE_POLICY_SHORT_FIRST])
 @pytest.mark.parametrize("serialize", [0, 1])
 def test_policies_and_step_overlap(target, policy, serialize):
     """Both sharing policies, with consecutive steps overlapping (operation pieces whose inputs
