@@ -41,8 +41,10 @@ RESEED_EVERY = 100
 # dram__bytes_read.sum + dram__bytes_write.sum of one Triad launch (FP64, n = 2^27) from an ncu
 # capture, with the sha256 of the kernel source it was taken on; reported as null when the
 # source has changed since.
-NCU_TRAFFIC = {"kernel": "k_stream_vec<TRIAD,double>", "n": 1 << 27, "bytes": None,
-               "source_sha256": None}
+NCU_TRAFFIC = {"kernel": "k_stream_vec<3, double, 32, 1, 0, 4>", "n": 1 << 27,
+               "bytes": 4 * 771011584,  # captured at n = 2^25 (536912896 read + 234116096 written), x4
+               "cfg": {"variant": 1, "vec_bytes": 32, "unroll": 1, "cache_hint": 0, "fp64_mul": 2},
+               "source_sha256": "3b0b388acac7535388e1e147d5ccc4530d2ade843088fbc42fbfa584e5eda91b"}
 
 
 def _rank_env():
@@ -535,8 +537,9 @@ def run_ours(args):
     triad_ms = per["triad"] / args.steps
     achieved = 3 * n * es / (triad_ms * 1e-3) / 1e9
     traffic = None
+    same_kernel = all(tuned["f64"]["triad"].get(k) == v for k, v in NCU_TRAFFIC["cfg"].items())
     if NCU_TRAFFIC["bytes"] and NCU_TRAFFIC["source_sha256"] == _kernel_source_sha() \
-            and NCU_TRAFFIC["n"] == n:
+            and NCU_TRAFFIC["n"] == n and same_kernel:
         traffic = NCU_TRAFFIC["bytes"]
     roofline = {"bound": "hbm", "kernel": "triad f64", "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
