@@ -43,7 +43,7 @@ RESEED_EVERY = 100
 # source has changed since.
 NCU_TRAFFIC = {"kernel": "k_stream_vec<3, double, 32, 1, 0, 4>", "n": 1 << 27,
                "bytes": 4 * 771011584,  # captured at n = 2^25 (536912896 read + 234116096 written), x4
-               "cfg": {"variant": 1, "vec_bytes": 32, "unroll": 1, "cache_hint": 0, "fp64_mul": 2},
+               "cfg": {"variant": 1, "vec_bytes": 32, "unroll": 1, "cache_hint": 1, "fp64_mul": 2},
                "source_sha256": "3b0b388acac7535388e1e147d5ccc4530d2ade843088fbc42fbfa584e5eda91b"}
 
 
@@ -394,6 +394,99 @@ def served_section(sx, torch, t, stream, args, rank):
     return out
 
 
+def fused_section(sx, torch, t, stream, n, rank, passes=100):
+    """The workload's 100 FP64 passes as 4 launches per pass vs one fused kernel (the same
+    roundings per element; bit-identical results, checked here on the whole arrays)."""
+    import stream_inputs as si
+    arrs = {}
+    for tag in ("iter", "fused"):
+        arrs[tag] = [sx.sx_alloc(t, sx.SX_F64, n) for _ in range(3)]
+        for k, arr in enumerate(arrs[tag]):
+            sx.sx_seed_uniform(arr, si.array_seed(si.BASE_SEED, k, rank), -1.0, 1.0)
+    e = sx.sx_executor_create(t, sx.SX_PAR_TASK)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    sx.sx_stream_iter(e, *arrs["iter"], Q, passes)
+    ev[1].record(stream)
+    ev[2].record(stream)
+    sx.sx_stream_fused(e, *arrs["fused"], Q, passes)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    t_iter, t_fused = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    same = True
+    for a1, a2 in zip(arrs["iter"], arrs["fused"]):
+        h1, h2 = np.empty(n, np.float64), np.empty(n, np.float64)
+        sx.sx_copy_d2h(h1.ctypes.data, a1, n)
+        sx.sx_copy_d2h(h2.ctypes.data, a2, n)
+        same &= bool(np.array_equal(h1.view(np.uint64), h2.view(np.uint64)))
+    for tag in arrs:
+        for arr in arrs[tag]:
+            sx.sx_free(arr)
+    sx.sx_executor_destroy(e)
+    stream_bytes = 10.0 * n * 8 * passes
+    return {"passes": passes, "four_launches_ms": round(t_iter, 3), "fused_ms": round(t_fused, 3),
+            "speedup": round(t_iter / t_fused, 3),
+            "four_launches_GB/s": round(stream_bytes / (t_iter * 1e-3) / 1e9, 1),
+            "fused_STREAM-equivalent_GB/s": round(stream_bytes / (t_fused * 1e-3) / 1e9, 1),
+            "fused_dram_bytes": 4 * n * 8, "bit_identical": same}
+
+
+def run_sweep(args):
+    """Size sweep (the paper's array-size figure): n = 2^lo..2^hi per array, FP64 and FP32, the
+    four kernels, VECTOR vs BULK (TMA bulk-copy staging) at fixed launch shapes.  Prints one
+    JSON line.  Back-to-back launches on the same arrays: below ~2^22-2^23 elements the three
+    arrays stay in the 126 MB L2."""
+    import torch
+    import paper_2206_06302_b300 as sx
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    t = sx.target_on_torch_stream(0, stream)
+    shapes = {
+        "vector": dict(variant=sx.SX_VARIANT_VECTOR, threads=256, vec_bytes=32, unroll=2, fp64_mul=2),
+        "bulk": dict(variant=sx.SX_VARIANT_BULK, threads=256, blocks_per_sm=1, tile_bytes=16384,
+                     stages=4, fp64_mul=2),
+    }
+    execs = {k: sx.sx_executor_create(t, sx.SX_PAR_TASK, v) for k, v in shapes.items()}
+    ops = (("copy", sx.SX_OP_COPY, 2), ("scale", sx.SX_OP_SCALE, 2), ("add", sx.SX_OP_ADD, 3),
+           ("triad", sx.SX_OP_TRIAD, 3))
+    rows = []
+    for dcode, dname, es in ((sx.SX_F64, "f64", 8), (sx.SX_F32, "f32", 4)):
+        nmax = 1 << args.sweep_hi
+        arrs = [sx.sx_alloc(t, dcode, nmax) for _ in range(3)]
+        for k, arr in enumerate(arrs):
+            sx.sx_seed_uniform(arr, k + 1, -1.0, 1.0)
+        base = [sx.sx_array_data(a)[0] for a in arrs]
+        for lg in range(args.sweep_lo, args.sweep_hi + 1):
+            n = 1 << lg
+            views = [sx.sx_array_wrap(t, dcode, p, n) for p in base]
+            x, y, o = views
+            for name, op, narr in ops:
+                for vname, e in execs.items():
+                    nbytes = narr * n * es
+                    reps = int(min(2000, max(5, 4e-3 / max(nbytes / 6e12, 2e-6))))
+                    for _ in range(3):
+                        sx.sx_execute_async(e, op, x, y, o, Q, future=False)
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev0.record(stream)
+                    for _ in range(reps):
+                        sx.sx_execute_async(e, op, x, y, o, Q, future=False)
+                    ev1.record(stream)
+                    ev1.synchronize()
+                    ms = ev0.elapsed_time(ev1) / reps
+                    rows.append({"dtype": dname, "log2n": lg, "op": name, "variant": vname,
+                                 "us": round(ms * 1e3, 2), "GB/s": round(nbytes / (ms * 1e-3) / 1e9, 1)})
+            for v in views:
+                sx.sx_free(v)
+        for a in arrs:
+            sx.sx_free(a)
+    sx.sx_target_synchronize(t)
+    print(json.dumps({"sweep": rows, "shapes": shapes,
+                      "note": "per-launch device time, back-to-back launches on the same arrays"}),
+          flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import paper_2206_06302_b300 as sx
@@ -412,12 +505,14 @@ def run_ours(args):
     names = (("copy", sx.SX_OP_COPY), ("scale", sx.SX_OP_SCALE), ("add", sx.SX_OP_ADD),
              ("triad", sx.SX_OP_TRIAD))
     tuned = {}
-    if args.tune_cache and os.path.exists(args.tune_cache):
-        sx.sx_tune_load(args.tune_cache)
+    # the autotuner's table: the committed one for this device, then --tune-cache on top of it
+    for path in (args.tune_table, args.tune_cache):
+        if path and os.path.exists(path):
+            sx.sx_tune_load(path)
     if args.tune:
         for dcode in (sx.SX_F64, sx.SX_F32):
             for name, op in names:
-                if sx.sx_tune_lookup(t, op, dcode, tune_n) is None:
+                if args.retune or sx.sx_tune_lookup(t, op, dcode, tune_n) is None:
                     sx.sx_tune(t, op, dcode, tune_n)
         if args.tune_cache:
             sx.sx_tune_save(args.tune_cache)
@@ -526,6 +621,9 @@ def run_ours(args):
     if not args.quick and "served" in args.sections:
         extra["served"] = served_section(sx, torch, t, stream, args, rank)
 
+    if not args.quick:
+        extra["fused_100_passes"] = fused_section(sx, torch, t, stream, n, rank)
+
     # ---- CPU oracle on a bounded sample (rank 0, N=1 only) ------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -579,9 +677,16 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=1 << 27)
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the step benchmark: the size sweep, vector vs TMA bulk staging")
+    ap.add_argument("--sweep-lo", type=int, default=10)
+    ap.add_argument("--sweep-hi", type=int, default=29)
     ap.add_argument("--ref-n", type=int, default=1 << 22)
     ap.add_argument("--no-tune", dest="tune", action="store_false")
-    ap.add_argument("--tune-cache", default="")
+    ap.add_argument("--tune-cache", default="", help="extra tuner table to load and to save to")
+    ap.add_argument("--tune-table", default=os.path.join(ROOT, "paper_2206_06302_b300", "tune_b300.json"),
+                    help="tuner table loaded first (the one shipped for B300)")
+    ap.add_argument("--retune", action="store_true", help="tune every pass kernel again")
     ap.add_argument("--tune-n", type=int, default=0,
                     help="size whose tuned launch shapes the pass kernels use (default: --n)")
     ap.add_argument("--quick", action="store_true", help="FP64 pass only (no FP32, e2e, sections)")
@@ -600,6 +705,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 
