@@ -52,6 +52,18 @@ def _rank_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def job_throughput(dist, local_ms, bytes_per_rank_step, steps, world, device):
+    """Whole-job throughput (GB/s) of a weak-scaling run: every rank moved `bytes_per_rank_step`
+    per step; the job's time is the slowest rank's.  Returns (GB/s, max time in ms)."""
+    ms = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    return world * bytes_per_rank_step * steps / (ms * 1e-3) / 1e9, ms
+
+
 def _measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -546,12 +558,8 @@ def run_ours(args):
             per[name] += events[s][k].elapsed_time(events[s][k + 1])
     # sum of the passes' own device times (re-construction every 100 passes falls between them)
     total_ms = sum(events[s][0].elapsed_time(events[s][4]) for s in range(args.steps))
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
     step_bytes = 10.0 * n * es
-    value = world * step_bytes * args.steps / (total_ms * 1e-3) / 1e9
+    value, total_ms = job_throughput(dist, total_ms, step_bytes, args.steps, world, "cuda")
     bytes_per = {"copy": 2, "scale": 2, "add": 3, "triad": 3}
     kernels = {}
     for name in per:
@@ -601,11 +609,8 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             sx.sx_stream_host(esync, *(h.data_ptr() for h in host), *dev, Q, 1)
         el = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([el], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
-        e2e = {"value": round(world * step_bytes * args.e2e_steps / el / 1e9, 2), "unit": "GB/s",
+        e2e_gbs, el_ms = job_throughput(dist, el * 1e3, step_bytes, args.e2e_steps, world, "cuda")
+        e2e = {"value": round(e2e_gbs, 2), "unit": "GB/s",
                "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 3 * n * 8,
                "steps": args.e2e_steps,
                "what": "sx_stream_host: h2d a,b,c + one pass (4 launches) + d2h a,b,c, host clock"}

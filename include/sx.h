@@ -146,6 +146,11 @@ int sx_target_stream(const sx_target *t, void **stream);
 /* Wait for all work on the target's stream, then check the device error word that bounded
  * device-side waits set (SX_ERR_DEVICE if one expired; the word is then cleared). */
 int sx_target_synchronize(sx_target *t);
+/* Self-test of the device-side failure path: enqueues a kernel whose bounded wait on a flag that
+ * nothing sets runs out after limit_us microseconds (1..1000000).  It records its code in the
+ * target's device error word, so the next sx_target_synchronize returns SX_ERR_DEVICE (and clears
+ * the word); the context stays usable.  Returns once the kernel is enqueued. */
+int sx_target_selftest(sx_target *t, int64_t limit_us);
 
 /* ---- arrays and the allocator: Section 3.2, Listing 1 (allocator_traits::target,
  *      bulk_construct, bulk_destroy) and Section 4.2 (construction offloaded to the GPU) ---- */

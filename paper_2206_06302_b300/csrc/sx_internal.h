@@ -153,6 +153,8 @@ int validate_bulk_cfg(const sx_target *t, int op, const sx_launch_cfg &cfg);
 sx_launch_cfg resolve_cfg(const sx_target *t, int op, int dtype, size_t n, const sx_launch_cfg *req);
 // Checks a fully specified configuration; SX_ERR_INVALID with a message if unsupported.
 int validate_cfg(const sx_target *t, int op, const sx_launch_cfg &cfg);
+// Enqueues the failure-path self-test kernel (sx_target_selftest).
+int launch_selftest(const sx_target *t, cudaStream_t stream, int64_t limit_us);
 // Reads and clears the target's device error word.
 int check_device_error(const sx_target *t);
 

@@ -250,6 +250,13 @@ int sx_target_synchronize(sx_target *t) {
     return sync_target(t);
 }
 
+int sx_target_selftest(sx_target *t, int64_t limit_us) {
+    if (!t) return fail(SX_ERR_INVALID, "target is NULL");
+    if (limit_us < 1 || limit_us > 1000000) return fail(SX_ERR_INVALID, "limit_us=%lld out of [1, 1e6]", (long long)limit_us);
+    DeviceScope ds(t->device);
+    return launch_selftest(t, t->stream, limit_us);
+}
+
 // ---- arrays / allocator ----------------------------------------------------------------------
 int sx_alloc(sx_target *t, sx_dtype dtype, size_t n, sx_array **out) {
     if (!t || !out) return fail(SX_ERR_INVALID, "NULL argument");

@@ -116,6 +116,7 @@ _PROTOS = {
     "sx_target_info_get": [P, C.POINTER(sx_target_info)],
     "sx_target_stream": [P, PP],
     "sx_target_synchronize": [P],
+    "sx_target_selftest": [P, C.c_int64],
     "sx_alloc": [P, I, SZ, PP],
     "sx_array_wrap": [P, I, P, SZ, PP],
     "sx_free": [P],
@@ -258,6 +259,10 @@ def sx_target_stream(t) -> int:
 
 def sx_target_synchronize(t) -> None:
     _check(lib.sx_target_synchronize(t), "sx_target_synchronize")
+
+
+def sx_target_selftest(t, limit_us: int) -> None:
+    _check(lib.sx_target_selftest(t, limit_us), "sx_target_selftest")
 
 
 def sx_alloc(t, dtype: int, n: int):

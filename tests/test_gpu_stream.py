@@ -378,3 +378,27 @@ def test_fused_product_units(target, mm):
     assert_bitwise(gb, b)
     assert_bitwise(gc, c)
     sx.sx_executor_destroy(e)
+
+
+def test_device_failure_path_selftest():
+    """A kernel's bounded wait that runs out reports SX_ERR_DEVICE at the next synchronisation
+    and leaves the context usable (no trap, no hang: the wait is limited to 2 ms)."""
+    t = sx.sx_target_create(0)
+    e = sx.sx_executor_create(t, sx.SX_PAR)
+    try:
+        sx.sx_target_selftest(t, 2000)
+        with pytest.raises(sx.SxError) as ei:
+            sx.sx_target_synchronize(t)
+        assert ei.value.status == sx.SX_ERR_DEVICE
+        sx.sx_target_synchronize(t)  # the word was cleared
+        x, y = _inputs(1000, np.float64, 9)
+        dx, dy, do = to_device(t, x), to_device(t, y), empty(t, np.float64, 1000)
+        sx.sx_transform_triad(e, dx, dy, do, 3.0)
+        assert_bitwise(to_host(do), oracle.triad(x, y, 3.0))
+        for a in (dx, dy, do):
+            sx.sx_free(a)
+        with pytest.raises(sx.SxError):
+            sx.sx_target_selftest(t, 0)
+    finally:
+        sx.sx_executor_destroy(e)
+        sx.sx_target_destroy(t)
