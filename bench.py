@@ -613,7 +613,8 @@ def run_ours(args):
         e2e = {"value": round(e2e_gbs, 2), "unit": "GB/s",
                "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 3 * n * 8,
                "steps": args.e2e_steps,
-               "what": "sx_stream_host: h2d a,b,c + one pass (4 launches) + d2h a,b,c, host clock"}
+               "what": "sx_stream_host: h2d a,b,c + one pass + d2h a,b,c from pinned host memory, "
+                       "pipelined in 32 MiB chunks over 3 streams; host clock"}
         for d in dev:
             sx.sx_free(d)
         sx.sx_executor_destroy(esync)

@@ -236,7 +236,10 @@ int sx_stream_iter(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double
 int sx_stream_fused(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double q, int iters);
 /* End to end from host memory: copy a, b, c (n elements, pinned or pageable host memory) to
  * the target's arrays, run `iters` passes of sx_stream_iter, copy the three arrays back.
- * Returns after the results are in host memory. */
+ * The work goes in 32 MiB chunks over three internal streams (every element's passes are
+ * independent), so copies in both directions and the kernels overlap; with pinned host memory
+ * the two link directions run at once.  Same bits as the unchunked sequence.  Returns after the
+ * results are in host memory. */
 int sx_stream_host(sx_executor *e, void *host_a, void *host_b, void *host_c, sx_array *a,
                    sx_array *b, sx_array *c, double q, int iters);
 

@@ -104,6 +104,10 @@ struct sx_target {
     std::string name;
     // Device error word: kernels whose bounded waits expire write a non-zero code here.
     int *d_err = nullptr;
+    // Streams and events of host<->device pipelines (sx_stream_host), created on first use.
+    static constexpr int kPipe = 3;
+    cudaStream_t pipe[kPipe] = {};
+    cudaEvent_t pipe_ev[kPipe + 1] = {};
 };
 
 struct sx_array {

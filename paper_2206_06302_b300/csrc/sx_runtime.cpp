@@ -2,6 +2,7 @@
 // of libsx (Sections 3.1-3.4 and 4.2 of Heller et al.; Listing 4 for sx_stream_iter).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
@@ -212,6 +213,10 @@ int sx_target_destroy(sx_target *t) {
         DeviceScope ds(t->device);
         cudaStreamSynchronize(t->stream);
         if (t->d_err) cudaFree(t->d_err);
+        for (auto &ps : t->pipe)
+            if (ps) cudaStreamDestroy(ps);
+        for (auto &pe : t->pipe_ev)
+            if (pe) cudaEventDestroy(pe);
         if (t->owns_stream) cudaStreamDestroy(t->stream);
     }
     delete t;
@@ -573,26 +578,61 @@ int sx_stream_fused(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, doubl
     return finish_call(e);
 }
 
+// Every element's chain of passes depends only on its own start values, so the work is cut into
+// chunks of elements, each copied in, run through `iters` passes and copied out on one of three
+// pipeline streams: host-to-device and device-to-host copies of different chunks then share the
+// two directions of the host link, and the kernels overlap both.  Results are the same bits as one
+// copy, `iters` whole-array passes and one copy back.
 int sx_stream_host(sx_executor *e, void *ha, void *hb, void *hc, sx_array *a, sx_array *b, sx_array *c,
                    double q, int iters) {
     SX_TRY(check_stream_arrays(e, a, b, c, iters));
     if (!ha || !hb || !hc) return fail(SX_ERR_INVALID, "host pointer is NULL");
-    DeviceScope ds(e->t->device);
-    const size_t bytes = a->n * dtype_size(a->dtype);
-    cudaStream_t s = e->t->stream;
-    SX_CUDA(cudaMemcpyAsync(a->ptr, ha, bytes, cudaMemcpyHostToDevice, s));
-    SX_CUDA(cudaMemcpyAsync(b->ptr, hb, bytes, cudaMemcpyHostToDevice, s));
-    SX_CUDA(cudaMemcpyAsync(c->ptr, hc, bytes, cudaMemcpyHostToDevice, s));
-    for (int k = 0; k < iters; ++k) {
-        SX_TRY(enqueue_op(e, SX_OP_COPY, a, nullptr, c, q));
-        SX_TRY(enqueue_op(e, SX_OP_SCALE, c, nullptr, b, q));
-        SX_TRY(enqueue_op(e, SX_OP_ADD, a, b, c, q));
-        SX_TRY(enqueue_op(e, SX_OP_TRIAD, b, c, a, q));
+    sx_target *t = e->t;
+    DeviceScope ds(t->device);
+    for (int i = 0; i < sx_target::kPipe; ++i)
+        if (!t->pipe[i]) SX_CUDA(cudaStreamCreateWithFlags(&t->pipe[i], cudaStreamNonBlocking));
+    for (auto &pe : t->pipe_ev)
+        if (!pe) SX_CUDA(cudaEventCreateWithFlags(&pe, cudaEventDisableTiming));
+    const size_t es = dtype_size(a->dtype);
+    const size_t n = a->n;
+    size_t chunk = ((size_t)32 << 20) / es;  // 32 MiB per array
+    chunk = std::max<size_t>(64, chunk / 64 * 64);
+    // the pipeline starts after the work already on the target's stream
+    SX_CUDA(cudaEventRecord(t->pipe_ev[sx_target::kPipe], t->stream));
+    for (int i = 0; i < sx_target::kPipe; ++i) SX_CUDA(cudaStreamWaitEvent(t->pipe[i], t->pipe_ev[sx_target::kPipe], 0));
+    char *pa = (char *)a->ptr, *pb = (char *)b->ptr, *pc = (char *)c->ptr;
+    char *qa = (char *)ha, *qb = (char *)hb, *qc = (char *)hc;
+    const sx_launch_cfg *fixed = e->fixed_cfg ? &e->cfg : nullptr;
+    size_t k = 0;
+    for (size_t off = 0; off < n; off += chunk, ++k) {
+        const size_t m = std::min(chunk, n - off);
+        const size_t ob = off * es, mb = m * es;
+        cudaStream_t s = t->pipe[k % sx_target::kPipe];
+        SX_CUDA(cudaMemcpyAsync(pa + ob, qa + ob, mb, cudaMemcpyHostToDevice, s));
+        SX_CUDA(cudaMemcpyAsync(pb + ob, qb + ob, mb, cudaMemcpyHostToDevice, s));
+        SX_CUDA(cudaMemcpyAsync(pc + ob, qc + ob, mb, cudaMemcpyHostToDevice, s));
+        const int ops[4] = {SX_OP_COPY, SX_OP_SCALE, SX_OP_ADD, SX_OP_TRIAD};
+        for (int it = 0; it < iters; ++it) {
+            for (int op : ops) {
+                const sx_launch_cfg cfg = resolve_cfg(t, op, a->dtype, m, fixed);
+                SX_TRY(validate_cfg(t, op, cfg));
+                // Listing 4's roles: copy a->c, scale c->b, add a,b->c, triad b,c->a
+                const void *x = op == SX_OP_COPY ? pa + ob : op == SX_OP_SCALE ? pc + ob : op == SX_OP_ADD ? pa + ob : pb + ob;
+                const void *y = op == SX_OP_ADD ? pb + ob : op == SX_OP_TRIAD ? pc + ob : nullptr;
+                void *o = op == SX_OP_COPY ? pc + ob : op == SX_OP_SCALE ? pb + ob : op == SX_OP_ADD ? pc + ob : pa + ob;
+                SX_TRY(launch_stream_op(t, s, op, a->dtype, x, y, o, m, q, cfg));
+            }
+        }
+        SX_CUDA(cudaMemcpyAsync(qa + ob, pa + ob, mb, cudaMemcpyDeviceToHost, s));
+        SX_CUDA(cudaMemcpyAsync(qb + ob, pb + ob, mb, cudaMemcpyDeviceToHost, s));
+        SX_CUDA(cudaMemcpyAsync(qc + ob, pc + ob, mb, cudaMemcpyDeviceToHost, s));
     }
-    SX_CUDA(cudaMemcpyAsync(ha, a->ptr, bytes, cudaMemcpyDeviceToHost, s));
-    SX_CUDA(cudaMemcpyAsync(hb, b->ptr, bytes, cudaMemcpyDeviceToHost, s));
-    SX_CUDA(cudaMemcpyAsync(hc, c->ptr, bytes, cudaMemcpyDeviceToHost, s));
-    return sync_target(e->t);
+    // the target's stream continues after the whole pipeline
+    for (int i = 0; i < sx_target::kPipe; ++i) {
+        SX_CUDA(cudaEventRecord(t->pipe_ev[i], t->pipe[i]));
+        SX_CUDA(cudaStreamWaitEvent(t->stream, t->pipe_ev[i], 0));
+    }
+    return sync_target(t);
 }
 
 int sx_transform_u8(sx_executor *e, int fn, const sx_array *in, sx_array *out) {

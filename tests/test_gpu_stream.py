@@ -402,3 +402,22 @@ def test_device_failure_path_selftest():
     finally:
         sx.sx_executor_destroy(e)
         sx.sx_target_destroy(t)
+
+
+def test_stream_host_pipelined_chunks(target, executor):
+    """End to end over several 32 MiB chunks on the pipeline streams, ragged last chunk, with the
+    target's own stream busy before and used after."""
+    for dt in (np.float64, np.float32):
+        n = (9 << 20) + 12345
+        a, b, c = si.stream_arrays(n, dt, base_seed=23)
+        ha, hb, hc = a.copy(), b.copy(), c.copy()
+        da, db, dc = (empty(target, dt, n) for _ in range(3))
+        sx.sx_bulk_construct(da, 7.0)  # queued on the target's stream before the pipeline
+        sx.sx_stream_host(executor, ha.ctypes.data, hb.ctypes.data, hc.ctypes.data, da, db, dc, 3.0, 2)
+        oracle.stream(a, b, c, 3.0, 2)
+        assert_bitwise(ha, a, "a")
+        assert_bitwise(hb, b, "b")
+        assert_bitwise(hc, c, "c")
+        assert_bitwise(to_host(da), a, "device a")
+        for h in (da, db, dc):
+            sx.sx_free(h)
