@@ -51,3 +51,116 @@ def test_full_size_stream_sampled(target, dt, variant):
     for a in arrs:
         sx.sx_free(a)
     sx.sx_executor_destroy(e)
+
+
+def _sampled(torch, buf, idx):
+    return buf.index_select(0, torch.from_numpy(idx.astype(np.int64)).cuda()).cpu().numpy()
+
+
+@pytest.mark.parametrize("op", ["copy", "triad"])
+def test_beyond_32bit_indices_fp32(target, op):
+    """n = 2^32 + 17 binary32 elements per array (17 GB each): indices past 2^32 and a ragged
+    tail, sampled against the oracle."""
+    import torch
+    n = (1 << 32) + 17
+    bufs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    torch.cuda.synchronize()
+    x, y, o = (sx.sx_array_wrap(target, sx.SX_F32, b.data_ptr(), n) for b in bufs)
+    sx.sx_seed_uniform(x, 31, -1.0, 1.0)
+    sx.sx_seed_uniform(y, 32, -1.0, 1.0)
+    e = sx.sx_executor_create(target, sx.SX_PAR)
+    sx.sx_execute(e, sx.SX_OP_COPY if op == "copy" else sx.SX_OP_TRIAD, x, y, o, 3.0)
+    idx = np.unique(np.concatenate([np.arange(0, 64), np.arange(n - 4096, n),
+                                    np.arange((1 << 32) - 64, (1 << 32) + 17),
+                                    np.random.default_rng(1).integers(0, n, 1 << 16)]))
+    xs = si.uniform_at(31, idx.astype(np.uint64), np.float32)
+    ys = si.uniform_at(32, idx.astype(np.uint64), np.float32)
+    assert_bitwise(_sampled(torch, bufs[0], idx), xs, "seeded x")
+    assert_bitwise(_sampled(torch, bufs[2], idx), oracle.apply(op, xs, ys, 3.0), op)
+    for a in (x, y, o):
+        sx.sx_free(a)
+    sx.sx_executor_destroy(e)
+    del bufs
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_largest_sweep_size_ragged(target, dt):
+    """The sweep's largest size plus a ragged tail, every kernel in the bench's launch shapes."""
+    import torch
+    n = (1 << 29) + 7
+    tdt = torch.float64 if dt == np.float64 else torch.float32
+    code = sx.SX_F64 if dt == np.float64 else sx.SX_F32
+    bufs = [torch.empty(n, dtype=tdt, device="cuda") for _ in range(3)]
+    torch.cuda.synchronize()
+    x, y, o = (sx.sx_array_wrap(target, code, b.data_ptr(), n) for b in bufs)
+    sx.sx_seed_uniform(x, 41, -1.0, 1.0)
+    sx.sx_seed_uniform(y, 42, -1.0, 1.0)
+    e = sx.sx_executor_create(target, sx.SX_PAR)
+    idx = np.unique(np.concatenate([np.arange(0, 64), np.arange(n - 300, n),
+                                    np.random.default_rng(2).integers(0, n, 1 << 16)]))
+    xs = si.uniform_at(41, idx.astype(np.uint64), dt)
+    ys = si.uniform_at(42, idx.astype(np.uint64), dt)
+    for name, op in (("copy", 0), ("scale", 1), ("add", 2), ("triad", 3)):
+        sx.sx_execute(e, op, x, y, o, 3.0)
+        assert_bitwise(_sampled(torch, bufs[2], idx), oracle.apply(name, xs, ys, 3.0), name)
+    for a in (x, y, o):
+        sx.sx_free(a)
+    sx.sx_executor_destroy(e)
+    del bufs
+    torch.cuda.empty_cache()
+
+
+def test_batched_workload_full_size(target):
+    """The 4096-instance batched workload (FP64 triad/add, n log-uniform in [2^10, 2^22], ~51 GB)
+    in one graph launch with its default shape: every 64th instance compared whole, and sampled
+    elements of every instance."""
+    inst = si.batched_instances(si.BASE_SEED, 4096)
+    offs, total = [], 0
+    for _, n in inst:
+        r = []
+        for _ in range(3):
+            total = (total + 255) // 256 * 256
+            r.append(total)
+            total += n * 8
+        offs.append(r)
+    buf = sx.sx_alloc(target, sx.SX_U8, total)
+    base = sx.sx_array_data(buf)[0]
+    seeds = []
+    for k, (_, n) in enumerate(inst):
+        for j in (0, 1):
+            seeds.append(sx.sx_batch_item(op=sx.SX_OP_SEED, dtype=sx.SX_F64, n=n, out=base + offs[k][j],
+                                          q=-1.0, q2=1.0, seed=si.array_seed(si.BASE_SEED, j, k)))
+    sb = sx.sx_batch_create(target, seeds)
+    sx.sx_batch_launch(sb)
+    sx.sx_target_synchronize(target)
+    sx.sx_batch_destroy(sb)
+    code = {"add": sx.SX_OP_ADD, "triad": sx.SX_OP_TRIAD}
+    items = [sx.sx_batch_item(op=code[op], dtype=sx.SX_F64, n=n, x=base + o[0], y=base + o[1],
+                              out=base + o[2], q=3.0) for (op, n), o in zip(inst, offs)]
+    b = sx.sx_batch_create(target, items)
+    sx.sx_batch_launch(b)
+    sx.sx_target_synchronize(target)
+    rng = np.random.default_rng(3)
+    for k, (op, n) in enumerate(inst):
+        whole = k % 64 == 0
+        if whole:
+            idx = np.arange(n)
+        else:
+            idx = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 8)]))
+        got = np.empty(idx.size, np.float64)
+        # element reads through borrowed single-element or whole views
+        if whole:
+            w = sx.sx_array_wrap(target, sx.SX_F64, base + offs[k][2], n)
+            sx.sx_copy_d2h(got.ctypes.data, w, n)
+            sx.sx_free(w)
+        else:
+            for m, i in enumerate(idx):
+                w = sx.sx_array_wrap(target, sx.SX_F64, base + offs[k][2] + 8 * int(i), 1)
+                sx.sx_copy_d2h(got[m:m + 1].ctypes.data, w, 1)
+                sx.sx_free(w)
+        xs = si.uniform_at(si.array_seed(si.BASE_SEED, 0, k), idx.astype(np.uint64), np.float64)
+        ys = si.uniform_at(si.array_seed(si.BASE_SEED, 1, k), idx.astype(np.uint64), np.float64)
+        assert_bitwise(got, oracle.apply(op, xs, ys, 3.0), f"instance {k} ({op}, n={n})")
+    sx.sx_batch_destroy(b)
+    sx.sx_free(buf)

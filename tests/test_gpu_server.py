@@ -156,3 +156,40 @@ def test_policies_and_step_overlap(target, policy, serialize):
     _check_all(s, ids, reqs, f"policy {policy} serialize {serialize}")
     assert sx.sx_server_stats_get(s)["steps"] > 10
     sx.sx_server_destroy(s)
+
+
+def test_served_full_size_requests(target):
+    """Requests of the served workload's upper sizes (up to 2^28 elements, 6 GiB of arrays each)
+    in a 64 GB arena, mixed with short ones, checked on sampled elements and whole short
+    outputs."""
+    import torch  # noqa: F401  (device already initialised by the target)
+    reqs = []
+    for k, n in enumerate([1 << 28, 3 << 25, 4096, 1 << 27, 12345, (1 << 26) + 3, 777, 1 << 20]):
+        reqs.append(dict(op=[sx.SX_OP_TRIAD, sx.SX_OP_SCALE, sx.SX_OP_ADD, sx.SX_OP_COPY][k % 4],
+                         dtype=sx.SX_F64 if k % 3 else sx.SX_F32, n=n, q=3.0,
+                         seed_x=int(si.word_scalar(77, 2 * k)), seed_y=int(si.word_scalar(77, 2 * k + 1)),
+                         lo=-1.0, hi=1.0))
+    s = sx.sx_server_create(target, budget_bytes=64 << 30)
+    ids = [sx.sx_server_submit(s, **r) for r in reqs]
+    rng = np.random.default_rng(4)
+    for rid, r in zip(ids, reqs):
+        st = sx.sx_server_wait(s, rid, 120000)
+        assert st["state"] == sx.SX_REQ_DONE
+        n, dt = r["n"], NP[r["dtype"]]
+        if n <= (1 << 20):
+            x, y, want = _expected(r)
+            assert np.array_equal(_read(s, rid, 2, r).view(np.uint8), want.view(np.uint8))
+        else:
+            idx = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 4096)]))
+            es = np.dtype(dt).itemsize
+            out = np.empty(idx.size, dt)
+            for m, i in enumerate(idx):  # single-element reads from the resident result
+                wrap = sx.sx_array_wrap(target, r["dtype"], st["out"] + es * int(i), 1)
+                sx.sx_copy_d2h(out[m:m + 1].ctypes.data, wrap, 1)
+                sx.sx_free(wrap)
+            xs = si.uniform_at(r["seed_x"], idx.astype(np.uint64), dt)
+            ys = si.uniform_at(r["seed_y"], idx.astype(np.uint64), dt)
+            want = oracle.apply(OPN[r["op"]], xs, ys, r["q"])
+            assert np.array_equal(out.view(np.uint8), want.view(np.uint8)), (rid, r["op"], n)
+        sx.sx_server_release(s, rid)
+    sx.sx_server_destroy(s)
