@@ -85,9 +85,9 @@ typedef enum sx_policy { SX_PAR = 1, SX_PAR_TASK = 2 } sx_policy;
 typedef enum sx_variant { SX_VARIANT_AUTO = 0, SX_VARIANT_VECTOR = 1, SX_VARIANT_BULK = 2 } sx_variant;
 
 /* Launch configuration of one algorithm call.  A zero field means "default".
- *   threads        threads per block (VECTOR: 128..1024, multiple of 32; BULK: 128..512)
+ *   threads        threads per block (multiple of 32; VECTOR: 32..1024; BULK: 32..1024)
  *   blocks_per_sm  VECTOR: grid = SMs * blocks_per_sm with a grid-stride loop; 0 = one tile
- *                  per block (grid covers the array).  BULK: persistent blocks per SM (1..2)
+ *                  per block (grid covers the array).  BULK: persistent blocks per SM (1..4)
  *   vec_bytes      VECTOR: 16 or 32 bytes per thread access
  *   unroll         VECTOR: vector accesses per thread per tile (1, 2 or 4)
  *   cache_hint     VECTOR: 0 = default caching, 1 = streaming (L1 no-allocate loads with an

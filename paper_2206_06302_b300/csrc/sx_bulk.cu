@@ -86,7 +86,7 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 template <int OP, class T, int MM>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
 k_stream_bulk(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t nbody,
               uint32_t tile_elems, int stages, T q, int *err) {
     constexpr bool HAS_Y = (OP == SX_OP_ADD || OP == SX_OP_TRIAD);
@@ -266,8 +266,8 @@ int dispatch_bulk(const sx_target *t, cudaStream_t s, int op, const void *x, con
 }  // namespace
 
 int validate_bulk_cfg(const sx_target *t, int op, const sx_launch_cfg &c) {
-    if (c.threads < 32 || c.threads > 512 || c.threads % 32)
-        return fail(SX_ERR_INVALID, "BULK threads=%d: need a multiple of 32 in [32, 512]", c.threads);
+    if (c.threads < 32 || c.threads > 1024 || c.threads % 32)
+        return fail(SX_ERR_INVALID, "BULK threads=%d: need a multiple of 32 in [32, 1024]", c.threads);
     if (c.tile_bytes < 1024 || c.tile_bytes > 65536 || c.tile_bytes % 1024)
         return fail(SX_ERR_INVALID, "BULK tile_bytes=%d: need a multiple of 1024 in [1024, 65536]", c.tile_bytes);
     if (c.stages < 2 || c.stages > kMaxStages)

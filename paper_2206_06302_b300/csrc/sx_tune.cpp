@@ -211,17 +211,18 @@ static std::vector<sx_launch_cfg> bulk_candidates(int op, int dtype) {
     std::vector<sx_launch_cfg> v;
     const int mm = mul64(op, dtype) ? 1 : 0;
     for (int tile : {8192, 16384, 32768})
-        for (int st : {2, 3, 4, 6})
-            for (int th : {128, 256}) {
-                sx_launch_cfg c{};
-                c.variant = SX_VARIANT_BULK;
-                c.threads = th;
-                c.blocks_per_sm = 1;
-                c.tile_bytes = tile;
-                c.stages = st;
-                c.fp64_mul = mm;
-                v.push_back(c);
-            }
+        for (int st : {3, 4, 6})
+            for (int th : {256, 512, 1024})
+                for (int bps : {1, 2}) {
+                    sx_launch_cfg c{};
+                    c.variant = SX_VARIANT_BULK;
+                    c.threads = th;
+                    c.blocks_per_sm = bps;
+                    c.tile_bytes = tile;
+                    c.stages = st;
+                    c.fp64_mul = mm;
+                    v.push_back(c);
+                }
     return v;
 }
 
