@@ -430,6 +430,12 @@ int step_slot_reserve(StepSlot &s, size_t items, size_t tiles) {
 constexpr uint32_t kStepMaxItems = 256;
 struct StepParams {
     uint32_t count, total_tiles;
+    // completion report (last launch of a step only): the block that finishes last writes `seq`
+    // to the host-mapped word `done`; `counter` is the step slot's device counter of finished
+    // blocks, left at zero for the slot's next use
+    uint64_t seq;
+    unsigned long long *done;
+    unsigned int *counter;
     uint32_t prefix[kStepMaxItems + 1];
     DevItem items[kStepMaxItems];
 };
@@ -463,12 +469,51 @@ __global__ void __launch_bounds__(1024) k_batch_step(const __grid_constant__ Ste
         run_tile<VB>(it, start, cnt);
     }
     if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (p.done) {
+        // every block's stores are issued; the last block to get here publishes the step
+        // (blocks exit only after the previous step completed, so the word only grows)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(p.counter, 1u) == gridDim.x - 1) {
+                *p.counter = 0u;
+                __threadfence_system();
+                *(volatile unsigned long long *)p.done = p.seq;
+            }
+        }
+    }
+}
+
+int step_warm(cudaStream_t stream) {
+    static thread_local StepParams p;
+    std::memset(&p, 0, sizeof p);  // no items, no tiles, no report: the kernel only returns
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(1);
+    lc.blockDim = dim3(32);
+    lc.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    SX_CUDA(cudaLaunchKernelEx(&lc, k_batch_step<16>, p));
+    SX_CUDA(cudaLaunchKernelEx(&lc, k_batch_step<32>, p));
+    SX_CUDA(cudaStreamSynchronize(stream));
+    return SX_OK;
 }
 
 int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const sx_batch_item *items, size_t count,
-                const sx_batch_cfg &cfg, const uint8_t *dependent, bool overlap) {
-    SX_TRY(step_slot_reserve(s, 0, 0));  // the completion event
+                const sx_batch_cfg &cfg, const uint8_t *dependent, bool overlap, const StepReport *report) {
+    if (!report) SX_TRY(step_slot_reserve(s, 0, 0));  // the completion event
     static thread_local StepParams p;   // 23 KB: kept off the stack
+    // the launch that carries the completion report: the last one that has work
+    size_t last = 0;
+    for (size_t first = 0; first < count; first += kStepMaxItems) {
+        const size_t m = std::min<size_t>(kStepMaxItems, count - first);
+        for (size_t i = 0; i < m; ++i)
+            if (items[first + i].n) last = first;
+    }
+    bool reported = false;
     for (size_t first = 0; first < count; first += kStepMaxItems) {
         const size_t m = std::min<size_t>(kStepMaxItems, count - first);
         uint32_t tiles = 0;
@@ -483,6 +528,11 @@ int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const sx_b
         p.count = (uint32_t)m;
         p.total_tiles = tiles;
         if (tiles == 0) continue;
+        const bool carries = report && first == last;
+        p.seq = carries ? report->seq : 0;
+        p.done = carries ? report->done : nullptr;
+        p.counter = carries ? report->counter : nullptr;
+        reported |= carries;
         uint64_t grid = (uint64_t)t->sm_count * cfg.blocks_per_sm;
         if (grid > tiles) grid = tiles;
         cudaLaunchConfig_t lc{};
@@ -498,7 +548,12 @@ int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const sx_b
         if (cfg.vec_bytes == 16) SX_CUDA(cudaLaunchKernelEx(&lc, k_batch_step<16>, p));
         else SX_CUDA(cudaLaunchKernelEx(&lc, k_batch_step<32>, p));
     }
-    SX_CUDA(cudaEventRecord(s.done, stream));
+    if (!report) {
+        SX_CUDA(cudaEventRecord(s.done, stream));
+    } else if (!reported) {
+        // nothing ran: publish the step from the host side of the stream's order
+        return fail(SX_ERR_INVALID, "step without work");
+    }
     return SX_OK;
 }
 

@@ -178,8 +178,20 @@ size_t step_tile_count(const sx_batch_item *items, size_t count, int tile_bytes)
 // parameters) on `stream` and record s.done after it.  With `overlap` the launch may start while
 // the previous step still runs (programmatic dependent launch); items with dependent[i] != 0 wait
 // for the previous step to complete first.
+// With `report`, no event is recorded: the step's last block to finish writes report->seq to the
+// host-mapped word report->done (report->counter: a zeroed device counter owned by the caller's
+// slot).  The step must have work.
+struct StepReport {
+    uint64_t seq;
+    unsigned long long *done;  // device address of a host-mapped word
+    unsigned int *counter;
+};
 int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const sx_batch_item *items,
-                size_t count, const sx_batch_cfg &cfg, const uint8_t *dependent, bool overlap);
+                size_t count, const sx_batch_cfg &cfg, const uint8_t *dependent, bool overlap,
+                const StepReport *report = nullptr);
+// Launch the step kernels once with no work on `stream` and wait: module loading and other
+// first-launch costs are paid here rather than by the first step of a latency-bound caller.
+int step_warm(cudaStream_t stream);
 
 // ---- autotuner table (sx_tune.cpp) ------------------------------------------------------
 bool tune_table_lookup(const sx_target *t, int op, int dtype, size_t n, sx_launch_cfg *cfg);

@@ -152,6 +152,10 @@ struct sx_server {
     std::vector<Request *> active;
     std::deque<Step> inflight;
     std::vector<StepSlot> slots;
+    // CONTINUOUS completion reports: the host-mapped word the last block of each step writes its
+    // step number to, and one device counter of finished blocks per slot
+    unsigned long long *done_host = nullptr, *done_dev = nullptr;
+    unsigned int *counters = nullptr;
     std::vector<int> free_slots;
     std::vector<cudaEvent_t> free_events;
     uint64_t next_id = 1;
@@ -160,6 +164,7 @@ struct sx_server {
     // threads (other than the server's) waiting for or holding the lock: the server thread
     // neither spins nor polls the GPU with the lock held while this is non-zero
     std::atomic<int> contenders{0};
+    std::atomic<uint64_t> grants{0};  // lock acquisitions by such threads
     // bumped on every arrival and every release of arena memory: the server thread watches it
     // without the lock to know that admission has something to do
     std::atomic<uint64_t> arrivals{0};
@@ -177,6 +182,11 @@ struct sx_server {
 
 namespace sx {
 namespace {
+
+// True once the step numbered `seq` has completed (its last block wrote seq or later).
+bool step_reported(const sx_server *s, uint64_t seq) {
+    return *(volatile unsigned long long *)s->done_host >= seq;
+}
 
 // Large requests hold more than 1/16 of the arena.  At most kMaxLarge of them hold memory at a
 // time, so the rest of the arena stays open to smaller requests: under fair sharing a long
@@ -421,8 +431,9 @@ int launch_step(sx_server *s, bool *launched) {
     }
     items.swap(sorted);
     dep.swap(sdep);
+    const StepReport report{st.seq, s->done_dev, s->counters + slot};
     const int rc = step_launch(s->t, s->t->stream, s->slots[slot], items.data(), items.size(), s->kcfg,
-                               dep.data(), s->cfg.serialize_steps == 0);
+                               dep.data(), s->cfg.serialize_steps == 0, &report);
     if (rc != SX_OK) {
         s->free_slots.push_back(slot);
         return rc;
@@ -441,9 +452,17 @@ bool retire(sx_server *s) {
     bool any = false;
     while (!s->inflight.empty()) {
         Step &st = s->inflight.front();
-        cudaEvent_t ev = st.slot >= 0 ? s->slots[st.slot].done : st.ev;
-        const cudaError_t e = cudaEventQuery(ev);
-        if (e == cudaErrorNotReady) break;
+        cudaError_t e = cudaSuccess;
+        if (st.slot >= 0) {
+            if (!step_reported(s, st.seq)) {
+                // a failed launch never reports: surface its error instead of waiting forever
+                e = cudaStreamQuery(s->t->stream);
+                if (e == cudaErrorNotReady || e == cudaSuccess) break;
+            }
+        } else {
+            e = cudaEventQuery(st.ev);
+            if (e == cudaErrorNotReady) break;
+        }
         if (e != cudaSuccess) {
             s->error = SX_ERR_CUDA;
             s->error_msg = cudaGetErrorString(e);
@@ -511,16 +530,26 @@ void server_loop(sx_server *s) {
         if (s->stop && s->error != SX_OK && s->inflight.empty()) break;
         // Between passes the lock goes to any thread that asked for it: the server thread does
         // not take it back while one is announced (an unlock followed at once by a lock would
-        // win the race against the woken thread every time and starve submitters).
-        auto wait_contenders = [s]() {  // at most 100 us, so callers polling in a loop cannot starve it
+        // win the race against the woken thread every time and starve submitters).  Each thread
+        // announced when the wait starts gets one turn: the wait ends once as many acquisitions
+        // have happened (or nobody is left, or after 100 us), so a caller polling in a loop, which
+        // announces itself again at once, neither starves nor throttles the server.
+        auto give_turns = [s](int c0, uint64_t g0) {
             const double until = now_seconds() + 1e-4;
-            while (s->contenders.load(std::memory_order_acquire) && now_seconds() < until)
+            while (s->contenders.load(std::memory_order_acquire) &&
+                   s->grants.load(std::memory_order_acquire) - g0 < (uint64_t)c0 && now_seconds() < until)
                 std::this_thread::yield();
         };
-        auto let_others_in = [s, &lk, &wait_contenders]() {
-            if (!s->contenders.load(std::memory_order_acquire)) return;
+        auto wait_contenders = [s, &give_turns]() {  // lock not held
+            const int c0 = s->contenders.load(std::memory_order_acquire);
+            if (c0) give_turns(c0, s->grants.load(std::memory_order_acquire));
+        };
+        auto let_others_in = [s, &lk, &give_turns]() {  // lock held
+            const int c0 = s->contenders.load(std::memory_order_acquire);
+            if (!c0) return;
+            const uint64_t g0 = s->grants.load(std::memory_order_acquire);
             lk.unlock();
-            wait_contenders();
+            give_turns(c0, g0);
             lk.lock();
         };
         if (launched || retired) {
@@ -532,9 +561,11 @@ void server_loop(sx_server *s) {
             // GPU busy: wait for the oldest step without the lock; come back early for arrivals
             // or freed memory (admission), and let callers that want the lock have it
             Step &front = s->inflight.front();
-            cudaEvent_t ev = front.slot >= 0 ? s->slots[front.slot].done : front.ev;
+            const bool by_word = front.slot >= 0;
+            const uint64_t want = front.seq;
+            cudaEvent_t ev = front.ev;
             lk.unlock();
-            while (cudaEventQuery(ev) == cudaErrorNotReady &&
+            while (!(by_word ? step_reported(s, want) : cudaEventQuery(ev) != cudaErrorNotReady) &&
                    s->arrivals.load(std::memory_order_acquire) == seen)
                 std::this_thread::yield();
             wait_contenders();
@@ -567,6 +598,7 @@ struct ApiLock {
     explicit ApiLock(sx_server *sv) : s(sv) {
         s->contenders.fetch_add(1, std::memory_order_relaxed);
         lk = std::unique_lock<std::mutex>(s->mu);
+        s->grants.fetch_add(1, std::memory_order_release);
     }
     ~ApiLock() {
         if (lk.owns_lock()) lk.unlock();
@@ -685,6 +717,30 @@ int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out) {
     if (c.mode == SX_SERVE_CONTINUOUS) {
         s->slots.resize(c.steps_in_flight);
         for (int i = c.steps_in_flight - 1; i >= 0; --i) s->free_slots.push_back(i);
+        cudaError_t e2 = cudaHostAlloc((void **)&s->done_host, sizeof(unsigned long long), cudaHostAllocMapped);
+        if (e2 == cudaSuccess) e2 = cudaHostGetDevicePointer((void **)&s->done_dev, s->done_host, 0);
+        if (e2 == cudaSuccess) e2 = cudaMalloc(&s->counters, c.steps_in_flight * sizeof(unsigned int));
+        if (e2 == cudaSuccess) e2 = cudaMemset(s->counters, 0, c.steps_in_flight * sizeof(unsigned int));
+        if (e2 != cudaSuccess) {
+            if (s->done_host) cudaFreeHost(s->done_host);
+            if (s->counters) cudaFree(s->counters);
+            cudaStreamDestroy(s->read_stream);
+            cudaFree(s->base);
+            t->used -= c.budget_bytes;
+            delete s;
+            return cuda_fail(e2, "server step reports");
+        }
+        *(volatile unsigned long long *)s->done_host = 0;
+        const int rc = step_warm(t->stream);
+        if (rc != SX_OK) {
+            cudaFreeHost(s->done_host);
+            cudaFree(s->counters);
+            cudaStreamDestroy(s->read_stream);
+            cudaFree(s->base);
+            t->used -= c.budget_bytes;
+            delete s;
+            return rc;
+        }
     }
     s->th = std::thread(server_loop, s);
     *out = s;
@@ -854,6 +910,8 @@ int sx_server_destroy(sx_server *s) {
         DeviceScope ds(s->t->device);
         cudaStreamSynchronize(s->t->stream);
         for (auto &sl : s->slots) step_slot_free(sl);
+        if (s->done_host) cudaFreeHost(s->done_host);
+        if (s->counters) cudaFree(s->counters);
         for (auto ev : s->free_events) cudaEventDestroy(ev);
         if (s->read_stream) cudaStreamDestroy(s->read_stream);
         cudaFree(s->base);
