@@ -77,15 +77,18 @@ __device__ __forceinline__ void tile_vector(const DevItem &it, uint64_t start, u
     const char *xb = reinterpret_cast<const char *>(x + head);
     const char *yb = HY ? reinterpret_cast<const char *>(y + head) : nullptr;
     char *ob = reinterpret_cast<char *>(o + head);
-    // two vectors per thread in flight per input
-    for (uint64_t v = threadIdx.x; v < nvec; v += 2 * (uint64_t)blockDim.x) {
+    // 32 bytes per input in flight per thread: two 16-byte vectors or one 32-byte vector (one
+    // 16-byte vector with the integer product).  More would raise the register demand of the
+    // whole kernel, which holds every op's tile code, past 64 and make it spill.
+    constexpr uint64_t PER = (MM == 0 && VB == 16) ? 2 : 1;
+    for (uint64_t v = threadIdx.x; v < nvec; v += PER * blockDim.x) {
         const uint64_t v2 = v + blockDim.x;
         uint64_t xa[W], ya[W], xc[W], yc[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) ya[k] = yc[k] = 0;
         ldv<VB, 0>(xb + v * VB, xa);
         if constexpr (HY) ldv<VB, 0>(yb + v * VB, ya);
-        const bool two = v2 < nvec;
+        const bool two = PER == 2 && v2 < nvec;
         if (two) {
             ldv<VB, 0>(xb + v2 * VB, xc);
             if constexpr (HY) ldv<VB, 0>(yb + v2 * VB, yc);
@@ -102,20 +105,13 @@ __device__ __forceinline__ void tile_vector(const DevItem &it, uint64_t start, u
     }
 }
 
-template <class T>
+// Seeded construction of a tile by the block's threads (seed_range); PM1: lo = -1, hi = 1.
+template <class T, bool PM1>
 __device__ __forceinline__ void tile_seed(const DevItem &it, uint64_t start, uint64_t cnt) {
-    T *o = static_cast<T *>(it.out) + start;
     const T lo = (T)it.q;
     const T span = (T)it.q2 - lo;  // RN(hi - lo) in T, as the host-side generator defines it
-    for (uint64_t e = threadIdx.x; e < cnt; e += blockDim.x)
-        o[e] = seeded_value(splitmix_word(it.seed, it.index_base + start + e), lo, span);
-}
-
-// Binary64 construction for lo = -1, hi = 1 on the integer units (see seeded_value_pm1).
-__device__ __forceinline__ void tile_seed_pm1(const DevItem &it, uint64_t start, uint64_t cnt) {
-    double *o = static_cast<double *>(it.out) + start;
-    for (uint64_t e = threadIdx.x; e < cnt; e += blockDim.x)
-        o[e] = seeded_value_pm1(splitmix_word(it.seed, it.index_base + start + e));
+    seed_range<T, PM1>(static_cast<T *>(it.out) + start, cnt, it.seed, it.index_base + start, lo, span,
+                       threadIdx.x, blockDim.x);
 }
 
 template <int VB>
@@ -143,9 +139,9 @@ __device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint
             else tile_vector<SX_OP_TRIAD, double, VB, 0>(it, start, cnt);
             break;
         case SX_OP_SEED:
-            if (f64 && it.q == -1.0 && it.q2 == 1.0) tile_seed_pm1(it, start, cnt);
-            else if (f64) tile_seed<double>(it, start, cnt);
-            else tile_seed<float>(it, start, cnt);
+            if (f64 && it.q == -1.0 && it.q2 == 1.0) tile_seed<double, true>(it, start, cnt);
+            else if (f64) tile_seed<double, false>(it, start, cnt);
+            else tile_seed<float, false>(it, start, cnt);
             break;
         default: break;
     }

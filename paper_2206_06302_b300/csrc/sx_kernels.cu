@@ -193,22 +193,18 @@ int dispatch_op(const sx_target *t, cudaStream_t s, int op, const void *x, const
 }
 
 // ---- seeded bulk construction ---------------------------------------------------------------
-// PM1: lo = -1, hi = 1, assembled on the integer units (seeded_value_pm1); otherwise the
-// generic formula on the FP64 pipe.
-template <bool PM1>
-__global__ void k_seed_f64(double *out, uint64_t n, uint64_t seed, double lo, double span, uint64_t base) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t w = splitmix_word(seed, base + i);
-        out[i] = PM1 ? seeded_value_pm1(w) : seeded_value(w, lo, span);
-    }
+// All threads of the grid share the range (seed_range); PM1: lo = -1, hi = 1 in binary64.
+template <class T, bool PM1>
+__global__ void __launch_bounds__(256) k_seed(T *out, uint64_t n, uint64_t seed, T lo, T span, uint64_t base) {
+    seed_range<T, PM1>(out, n, seed, base, lo, span, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                       (uint64_t)gridDim.x * blockDim.x);
 }
 
-__global__ void k_seed_f32(float *out, uint64_t n, uint64_t seed, float lo, float span, uint64_t base) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        out[i] = seeded_value(splitmix_word(seed, base + i), lo, span);
-    }
+// Blocks of 256 threads for `n` elements taken `per_thread` at a time: up to 8 per SM.
+unsigned seed_blocks(size_t n, int per_thread) {
+    uint64_t b = (n + 256ull * per_thread - 1) / (256ull * per_thread);
+    if (b > 148ull * 8) b = 148ull * 8;
+    return b == 0 ? 1u : (unsigned)b;
 }
 
 template <class T>
@@ -382,17 +378,17 @@ int launch_fill(cudaStream_t s, int dtype, void *out, size_t n, double value) {
 int launch_seed(cudaStream_t s, int dtype, void *out, size_t n, uint64_t seed, double lo, double hi,
                 uint64_t index_base) {
     if (n == 0) return SX_OK;
-    const unsigned b = setup_blocks(n);
     if (dtype == SX_F64) {
         const double span = hi - lo;
+        const unsigned b = seed_blocks(n, 8);
         if (lo == -1.0 && hi == 1.0)
-            k_seed_f64<true><<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
+            k_seed<double, true><<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
         else
-            k_seed_f64<false><<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
+            k_seed<double, false><<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
     } else if (dtype == SX_F32) {
         const float lo32 = (float)lo, hi32 = (float)hi;
         const float span = hi32 - lo32;
-        k_seed_f32<<<b, 256, 0, s>>>((float *)out, n, seed, lo32, span, index_base);
+        k_seed<float, false><<<seed_blocks(n, 16), 256, 0, s>>>((float *)out, n, seed, lo32, span, index_base);
     } else {
         return fail(SX_ERR_DTYPE, "seed_uniform takes F32 or F64 (got dtype %d)", dtype);
     }

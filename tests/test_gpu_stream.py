@@ -253,6 +253,76 @@ def test_seeded_construction_matches_generator(target, dt):
         sx.sx_free(d)
 
 
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_seeded_construction_misaligned(target, dt):
+    """Arrays that start off the 32-byte store alignment: scalar head, vector body, scalar tail."""
+    import torch
+    es = np.dtype(dt).itemsize
+    code = sx.SX_F64 if dt == np.float64 else sx.SX_F32
+    buf = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    for off in range(0, 32, es):
+        for n, lo, hi in ((1, -1.0, 1.0), (7, -1.0, 1.0), (70001, -1.0, 1.0), (4099, 0.5, 2.0)):
+            buf.zero_()
+            torch.cuda.synchronize()
+            d = sx.sx_array_wrap(target, code, buf.data_ptr() + 64 + off, n)
+            sx.sx_seed_uniform(d, 31 + off, lo, hi)
+            sx.sx_target_synchronize(target)
+            h = buf.cpu().numpy()
+            got = h[64 + off:64 + off + n * es].view(dt)
+            assert_bitwise(got, si.uniform(31 + off, n, dt, lo, hi), f"offset {off} n {n}")
+            assert not h[:64 + off].any() and not h[64 + off + n * es:].any(), "wrote outside the array"
+            sx.sx_free(d)
+
+
+def _small_k_indices(seed, count):
+    """Indices i < count whose word gives |k| < 2^32 for lo = -1, hi = 1 (k = (w >> 11) - 2^52,
+    the value k 2^-52): the words whose leading bit lies in the low half of k."""
+    w = si.words(seed, count)
+    k = (w >> np.uint64(11)).astype(np.int64) - (1 << 52)
+    return np.nonzero(np.abs(k) < (1 << 32))[0]
+
+
+def test_seeded_pm1_small_magnitudes(target):
+    """The lo = -1, hi = 1 binary64 construction has a separate path for |k| < 2^32 (about one
+    word in 2^20): such words, found by the host generator, must come out exact through the
+    grid-wide kernel and through batched tiles, at head, vector-body and tail positions."""
+    import torch
+    seed, count = 4242, 1 << 23
+    hits = _small_k_indices(seed, count)
+    assert hits.size >= 2, "no small-magnitude word in range"
+    n = int(hits[-1]) + 1
+    d = empty(target, np.float64, n)
+    sx.sx_seed_uniform(d, seed, -1.0, 1.0)
+    ref = si.uniform(seed, n, np.float64)
+    assert np.all(np.abs(ref[hits]) < 2.0 ** -20)
+    assert_bitwise(to_host(d), ref, "seed_uniform")
+    sx.sx_free(d)
+    # batched tiles: each hit at the start, inside and at the end of a small item, with the
+    # output at every 8-byte offset of the 32-byte vector alignment
+    buf = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    items, expect = [], []
+    at = 0
+    for h in hits[:4]:
+        for off in (0, 8, 16, 24):
+            for lead, m in ((0, 40), (17, 40), (39, 40), (3, 5)):
+                at = (at + 255) // 256 * 256 + off
+                items.append(sx.sx_batch_item(op=sx.SX_OP_SEED, dtype=sx.SX_F64, n=m,
+                                              out=buf.data_ptr() + at, q=-1.0, q2=1.0, seed=seed,
+                                              index_base=int(h) - lead))
+                expect.append((at, si.uniform(seed, m, np.float64, start=int(h) - lead)))
+                at += 8 * m
+    for cfg in (None, dict(chunk_bytes=16384, threads=64, blocks_per_sm=1, vec_bytes=16)):
+        buf.zero_()
+        torch.cuda.synchronize()
+        b = sx.sx_batch_create(target, items, cfg)
+        sx.sx_batch_launch(b)
+        sx.sx_target_synchronize(target)
+        sx.sx_batch_destroy(b)
+        h = buf.cpu().numpy()
+        for k, (o, e) in enumerate(expect):
+            assert_bitwise(h[o:o + 8 * e.size].view(np.float64), e, f"item {k}")
+
+
 def test_bulk_construct_fill(target):
     for dt in (np.float64, np.float32, np.uint8):
         d = empty(target, dt, 1001)
