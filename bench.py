@@ -10,8 +10,10 @@ ranks (weak scaling: every rank runs its own arrays; no collective on the data p
 Also reported on the same JSON line: per-kernel GB/s (FP64 and FP32), the roofline of the
 dominant kernel (Triad) against the measured HBM copy bandwidth, the end-to-end figure through
 the C ABI from pinned host buffers, the CPU oracle on a bounded sample, SM clocks sampled during
-the timed region, and (sections "batched" and "served") the persistent batched launcher vs one
-launch per instance and the continuous-batching server vs a per-call FIFO.
+the timed region, and the sections: "batched" (the persistent batched launcher vs one launch
+per instance), "served" (the continuous-batching server vs a per-call FIFO), "overlap" (STREAM
+sets on one stream vs one target and stream per set) and "copies" (host<->device copy
+bandwidth), plus the oracle's loops block-partitioned over the host cores.
 
 ``--impl reference`` times the CPU oracle (serial C, one core) on a bounded sample instead.
 """
@@ -444,6 +446,165 @@ def fused_section(sx, torch, t, stream, n, rank, passes=100):
             "fused_dram_bytes": 4 * n * 8, "bit_identical": same}
 
 
+def overlap_section(sx, torch, sets=4, passes=20, sizes=(1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24)):
+    """Asynchronous execution over several targets (Section 3.3 async_execute/bulk_async_execute,
+    Section 4.2: a target is a device and a stream).  `sets` independent FP64 STREAM array sets,
+    `passes` passes each, enqueued pass by pass with PAR_TASK executors and waited for at the end:
+    either every set on one target (one stream: the sets run one after another) or each set on a
+    target of its own (one stream each, free to overlap).  Same memory in both modes (the one-
+    stream mode borrows the sets' arrays).  Host clock from the first enqueue to the last wait;
+    results checked against the oracle (all elements up to 2^20, the first 4096 above)."""
+    import oracle
+    import stream_inputs as si
+    tgts = [sx.sx_target_create(0) for _ in range(sets)]
+    execs = [sx.sx_executor_create(tt, sx.SX_PAR_TASK) for tt in tgts]
+    rows = []
+    for n in sizes:
+        owned = [[sx.sx_alloc(tgts[k], sx.SX_F64, n) for _ in range(3)] for k in range(sets)]
+        borrowed = [[sx.sx_array_wrap(tgts[0], sx.SX_F64, sx.sx_array_data(a)[0], n) for a in owned[k]]
+                    for k in range(sets)]
+
+        def seed():
+            for k in range(sets):
+                for j, a in enumerate(owned[k]):
+                    sx.sx_seed_uniform(a, si.array_seed(si.BASE_SEED + 17, j, k), -1.0, 1.0)
+            for tt in tgts:
+                sx.sx_target_synchronize(tt)
+
+        def run(concurrent):
+            seed()
+            t0 = time.perf_counter()
+            for _ in range(passes):
+                for k in range(sets):
+                    if concurrent:
+                        sx.sx_stream_iter(execs[k], *owned[k], Q, 1)
+                    else:
+                        sx.sx_stream_iter(execs[0], *borrowed[k], Q, 1)
+            for ex in execs:
+                sx.sx_executor_wait(ex)
+            return time.perf_counter() - t0
+
+        def check():
+            m = n if n <= (1 << 20) else 4096
+            ok = True
+            for k in range(sets):
+                want = [si.uniform(si.array_seed(si.BASE_SEED + 17, j, k), m, np.float64) for j in range(3)]
+                oracle.stream(*want, Q, passes)
+                for j in range(3):
+                    got = np.empty(m, np.float64)
+                    sx.sx_copy_d2h(got.ctypes.data, owned[k][j], m)
+                    ok &= bool(np.array_equal(got.view(np.uint64), want[j].view(np.uint64)))
+            return ok
+
+        run(False)
+        run(True)  # warm both
+        one = min(run(False) for _ in range(3))
+        same = check()
+        many = min(run(True) for _ in range(3))
+        same &= check()
+        moved = 10.0 * n * 8 * passes * sets
+        rows.append({"n": n, "one_stream_ms": round(one * 1e3, 3), "stream_per_set_ms": round(many * 1e3, 3),
+                     "speedup": round(one / many, 3), "one_stream_GB/s": round(moved / one / 1e9, 1),
+                     "stream_per_set_GB/s": round(moved / many / 1e9, 1), "bit_identical": same})
+        for k in range(sets):
+            for a in borrowed[k] + owned[k]:
+                sx.sx_free(a)
+    for ex in execs:
+        sx.sx_executor_destroy(ex)
+    for tt in tgts:
+        sx.sx_target_destroy(tt)
+    return {"what": f"{sets} independent FP64 STREAM sets x {passes} passes, PAR_TASK, enqueued pass by pass; "
+                    "one target (one stream) vs one target per set; host clock incl. enqueue",
+            "runs": rows}
+
+
+def copies_section(sx, torch, t, sizes=(1 << 20, 1 << 24, 1 << 28, 1 << 30), reps=5):
+    """Host<->device copy algorithm (Section 4.2: copy between host and device is a CUDA memcpy)
+    through sx_copy_h2d / sx_copy_d2h on pinned and pageable host buffers, and both directions at
+    once (pinned; the two copies on two targets' streams).  Best of `reps`, host clock."""
+    rows = []
+    t2 = sx.sx_target_create(0)
+    for nbytes in sizes:
+        d1, d2 = sx.sx_alloc(t, sx.SX_U8, nbytes), sx.sx_alloc(t2, sx.SX_U8, nbytes)
+        pin1 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        pin2 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        page = np.ones(nbytes, np.uint8)
+
+        def best(fn):
+            fn()
+            ts = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                fn()
+                ts.append(time.perf_counter() - t0)
+            return min(ts)
+
+        def both():
+            sx.sx_copy_h2d_async(d1, pin1.data_ptr(), nbytes)
+            sx.sx_copy_d2h_async(pin2.data_ptr(), d2, nbytes)
+            sx.sx_target_synchronize(t)
+            sx.sx_target_synchronize(t2)
+
+        r = {"bytes": nbytes,
+             "h2d_pinned_GB/s": nbytes / best(lambda: sx.sx_copy_h2d(d1, pin1.data_ptr(), nbytes)) / 1e9,
+             "d2h_pinned_GB/s": nbytes / best(lambda: sx.sx_copy_d2h(pin1.data_ptr(), d1, nbytes)) / 1e9,
+             "h2d_pageable_GB/s": nbytes / best(lambda: sx.sx_copy_h2d(d1, page.ctypes.data, nbytes)) / 1e9,
+             "d2h_pageable_GB/s": nbytes / best(lambda: sx.sx_copy_d2h(page.ctypes.data, d1, nbytes)) / 1e9,
+             "both_directions_pinned_GB/s": 2 * nbytes / best(both) / 1e9}
+        rows.append({k: (round(v, 2) if isinstance(v, float) else v) for k, v in r.items()})
+        sx.sx_free(d1)
+        sx.sx_free(d2)
+        del pin1, pin2, page
+    sx.sx_target_destroy(t2)
+    return {"what": "sx_copy_h2d/d2h (synchronous) from pinned and pageable host memory; both directions "
+                    "at once on two streams (pinned); best of %d, host clock" % reps, "runs": rows}
+
+
+def cpu_oracle_threads_gbs(n: int, seconds: float):
+    """The oracle's STREAM pass with its loops block-partitioned over the host cores: thread k
+    runs the oracle on elements [n k / T, n (k + 1) / T) of each array, pinned to one core; a pass
+    ends when every block has finished (every element's pass is independent of the others')."""
+    import threading
+    import oracle
+    import stream_inputs as si
+    cpus = sorted(os.sched_getaffinity(0))
+    nt = len(cpus)
+    a, b, c = si.stream_arrays(n, np.float64)
+    oracle.default()
+    bounds = [(n * k // nt, n * (k + 1) // nt) for k in range(nt)]
+    start, end = threading.Barrier(nt + 1), threading.Barrier(nt + 1)
+    stop = [False]
+
+    def worker(k):
+        os.sched_setaffinity(0, {cpus[k]})
+        lo, hi = bounds[k]
+        while True:
+            start.wait()
+            if stop[0]:
+                return
+            oracle.stream(a[lo:hi], b[lo:hi], c[lo:hi], Q, 1)
+            end.wait()
+
+    ths = [threading.Thread(target=worker, args=(k,), daemon=True) for k in range(nt)]
+    for th in ths:
+        th.start()
+    start.wait()
+    end.wait()  # warm (page in)
+    passes, t0 = 0, time.perf_counter()
+    while True:
+        start.wait()
+        end.wait()
+        passes += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    stop[0] = True
+    start.wait()
+    for th in ths:
+        th.join()
+    return 10.0 * n * 8 * passes / el / 1e9, passes, el, nt
+
+
 def run_sweep(args):
     """Size sweep (the paper's array-size figure): n = 2^lo..2^hi per array, FP64 and FP32, the
     four kernels, VECTOR vs BULK (TMA bulk-copy staging) at fixed launch shapes.  Prints one
@@ -629,6 +790,10 @@ def run_ours(args):
 
     if not args.quick:
         extra["fused_100_passes"] = fused_section(sx, torch, t, stream, n, rank)
+    if not args.quick and "overlap" in args.sections:
+        extra["overlap_targets"] = overlap_section(sx, torch)
+    if not args.quick and "copies" in args.sections:
+        extra["copies"] = copies_section(sx, torch, t)
 
     # ---- CPU oracle on a bounded sample (rank 0, N=1 only) ------------------------------------
     cpu = None
@@ -637,6 +802,12 @@ def run_ours(args):
         cpu = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"STREAM FP64 pass on n={args.cpu_n} per array, {passes} passes "
                          f"in {el:.1f} s (serial C, -O2 -ffp-contract=off)"}
+        if args.cpu_threads_n:
+            gbs, passes, el, nt = cpu_oracle_threads_gbs(args.cpu_threads_n, args.cpu_seconds / 2)
+            extra["cpu_baseline_threads"] = {
+                "value": round(gbs, 3), "unit": "GB/s", "cores": nt, "kind": "oracle loops, block-partitioned",
+                "sample": f"STREAM FP64 pass on n={args.cpu_threads_n} per array, {passes} passes in "
+                          f"{el:.1f} s, one contiguous block per pinned thread"}
 
     triad_ms = per["triad"] / args.steps
     achieved = 3 * n * es / (triad_ms * 1e-3) / 1e9
@@ -700,7 +871,9 @@ def main(argv=None):
     ap.add_argument("--cpu-n", type=int, default=1 << 24)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--sections", default="batched,served")
+    ap.add_argument("--sections", default="batched,served,overlap,copies")
+    ap.add_argument("--cpu-threads-n", type=int, default=1 << 25,
+                    help="sample size of the threaded CPU baseline (0: skip)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-reps", type=int, default=10)
     ap.add_argument("--serve-count", type=int, default=2000)

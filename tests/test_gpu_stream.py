@@ -491,3 +491,43 @@ def test_stream_host_pipelined_chunks(target, executor):
         assert_bitwise(to_host(da), a, "device a")
         for h in (da, db, dc):
             sx.sx_free(h)
+
+
+def test_passes_on_several_targets_at_once():
+    """Asynchronous execution on several targets (one stream each): independent STREAM sets
+    enqueued pass by pass with PAR_TASK executors, futures on each target, then waited for; every
+    set equals its own serial oracle run, and a set borrowed by another target's executor gives
+    the same bits."""
+    sets, n, passes = 3, 100003, 4
+    tgts = [sx.sx_target_create(0) for _ in range(sets)]
+    execs = [sx.sx_executor_create(t, sx.SX_PAR_TASK) for t in tgts]
+    host = [si.stream_arrays(n, np.float64, base_seed=40 + k) for k in range(sets)]
+    dev = [[to_device(tgts[k], h) for h in host[k]] for k in range(sets)]
+    for _ in range(passes):
+        for k in range(sets):
+            sx.sx_stream_iter(execs[k], *dev[k], 3.0, 1)
+    futs = [sx.sx_execute_async(execs[k], sx.SX_OP_COPY, dev[k][0], None, dev[k][2], 0.0) for k in range(sets)]
+    for f in futs:
+        sx.sx_future_wait(f, 10000)
+        sx.sx_future_destroy(f)
+    for k in range(sets):
+        a, b, c = (h.copy() for h in host[k])
+        oracle.stream(a, b, c, 3.0, passes)
+        c = a.copy()
+        for got, want in zip(dev[k], (a, b, c)):
+            assert_bitwise(to_host(got), want, f"set {k}")
+    # the same memory through another target's executor
+    ptrs = [sx.sx_array_data(x)[0] for x in dev[1]]
+    borrowed = [sx.sx_array_wrap(tgts[0], sx.SX_F64, p, n) for p in ptrs]
+    a, b, c = (to_host(x) for x in dev[1])
+    sx.sx_stream_iter(execs[0], *borrowed, 3.0, 2)
+    sx.sx_executor_wait(execs[0])
+    oracle.stream(a, b, c, 3.0, 2)
+    for got, want in zip(dev[1], (a, b, c)):
+        assert_bitwise(to_host(got), want, "borrowed")
+    for x in borrowed + [x for d in dev for x in d]:
+        sx.sx_free(x)
+    for e in execs:
+        sx.sx_executor_destroy(e)
+    for t in tgts:
+        sx.sx_target_destroy(t)
