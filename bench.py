@@ -11,9 +11,10 @@ Also reported on the same JSON line: per-kernel GB/s (FP64 and FP32), the roofli
 dominant kernel (Triad) against the measured HBM copy bandwidth, the end-to-end figure through
 the C ABI from pinned host buffers, the CPU oracle on a bounded sample, SM clocks sampled during
 the timed region, and the sections: "batched" (the persistent batched launcher vs one launch
-per instance), "served" (the continuous-batching server vs a per-call FIFO), "overlap" (STREAM
-sets on one stream vs one target and stream per set) and "copies" (host<->device copy
-bandwidth), plus the oracle's loops block-partitioned over the host cores.
+per instance), "served" (the continuous-batching server vs a per-call FIFO), "small" (small
+arrays: direct launches vs CUDA graphs vs one fused kernel), "overlap" (STREAM sets on one
+stream vs one target and stream per set) and "copies" (host<->device copy bandwidth), plus the
+oracle's loops block-partitioned over the host cores.
 
 ``--impl reference`` times the CPU oracle (serial C, one core) on a bounded sample instead.
 """
@@ -446,6 +447,63 @@ def fused_section(sx, torch, t, stream, n, rank, passes=100):
             "fused_dram_bytes": 4 * n * 8, "bit_identical": same}
 
 
+def small_n_section(sx, torch, passes=100, sizes=(1 << 10, 1 << 14, 1 << 16, 1 << 18, 1 << 20, 1 << 22)):
+    """Small arrays, where a STREAM pass is bound by the cost of its four kernel launches (the
+    paper's small-size overhead): `passes` passes as `passes` single-pass calls (direct
+    launches), as one sx_stream_iter call (replayed from CUDA graphs), and fused into one kernel.
+    PAR_TASK executor on a target of its own, host clock from the first call to the wait (the
+    graph is captured by an untimed warm-up call); FP64; results checked against the oracle."""
+    import oracle
+    import stream_inputs as si
+    tt = sx.sx_target_create(0)
+    e = sx.sx_executor_create(tt, sx.SX_PAR_TASK)
+    rows = []
+    for n in sizes:
+        host = si.stream_arrays(n, np.float64, base_seed=55)
+        arrs = [sx.sx_alloc(tt, sx.SX_F64, n) for _ in range(3)]
+
+        def load():
+            for h, d in zip(host, arrs):
+                sx.sx_copy_h2d(d, h.ctypes.data, n)
+            sx.sx_target_synchronize(tt)
+
+        def timed(fn):
+            load()
+            t0 = time.perf_counter()
+            fn()
+            sx.sx_executor_wait(e)
+            return time.perf_counter() - t0
+
+        def direct():
+            for _ in range(passes):
+                sx.sx_stream_iter(e, *arrs, Q, 1)
+
+        modes = {"direct": direct, "graphs": lambda: sx.sx_stream_iter(e, *arrs, Q, passes),
+                 "fused": lambda: sx.sx_stream_fused(e, *arrs, Q, passes)}
+        res = {}
+        want = [h.copy() for h in host]
+        oracle.stream(*want, Q, passes)
+        same = True
+        for name, fn in modes.items():
+            timed(fn)  # warm (captures the graphs)
+            res[name] = min(timed(fn) for _ in range(3))
+            for d, w in zip(arrs, want):
+                got = np.empty(n, np.float64)
+                sx.sx_copy_d2h(got.ctypes.data, d, n)
+                same &= bool(np.array_equal(got.view(np.uint64), w.view(np.uint64)))
+        moved = 10.0 * n * 8 * passes
+        rows.append({"n": n, **{f"{k}_us_per_pass": round(v * 1e6 / passes, 2) for k, v in res.items()},
+                     **{f"{k}_GB/s": round(moved / v / 1e9, 1) for k, v in res.items()},
+                     "bit_identical": same})
+        for d in arrs:
+            sx.sx_free(d)
+    sx.sx_executor_destroy(e)
+    sx.sx_target_destroy(tt)
+    return {"what": f"FP64 STREAM, {passes} passes: {passes} single-pass calls (4 launches each) vs one "
+                    "call (CUDA graphs of 16 passes) vs one fused kernel; PAR_TASK, host clock incl. enqueue",
+            "runs": rows}
+
+
 def overlap_section(sx, torch, sets=4, passes=20, sizes=(1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24)):
     """Asynchronous execution over several targets (Section 3.3 async_execute/bulk_async_execute,
     Section 4.2: a target is a device and a stream).  `sets` independent FP64 STREAM array sets,
@@ -790,6 +848,8 @@ def run_ours(args):
 
     if not args.quick:
         extra["fused_100_passes"] = fused_section(sx, torch, t, stream, n, rank)
+    if not args.quick and "small" in args.sections:
+        extra["small_n_passes"] = small_n_section(sx, torch)
     if not args.quick and "overlap" in args.sections:
         extra["overlap_targets"] = overlap_section(sx, torch)
     if not args.quick and "copies" in args.sections:
@@ -871,7 +931,7 @@ def main(argv=None):
     ap.add_argument("--cpu-n", type=int, default=1 << 24)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--sections", default="batched,served,overlap,copies")
+    ap.add_argument("--sections", default="batched,served,small,overlap,copies")
     ap.add_argument("--cpu-threads-n", type=int, default=1 << 25,
                     help="sample size of the threaded CPU baseline (0: skip)")
     ap.add_argument("--batch-count", type=int, default=4096)

@@ -229,7 +229,11 @@ int sx_execute(sx_executor *e, sx_op op, const sx_array *x, const sx_array *y, s
 int sx_execute_async(sx_executor *e, sx_op op, const sx_array *x, const sx_array *y,
                      sx_array *out, double q, sx_future **fut);
 /* Listing 4's stream(): `iters` passes of Copy c=a, Scale b=c*q, Add c=a+b, Triad a=b+c*q,
- * four launches per pass in stream order.  Follows the executor's policy. */
+ * four kernels per pass in stream order.  Follows the executor's policy.  With iters >= 2 the
+ * passes are replayed from CUDA graphs of up to 16 passes, captured on the executor's first
+ * call for these arrays, q and launch shapes and kept by the executor (the 8 most recent), so
+ * that small arrays are not bound by per-kernel launch cost; same kernels, same bits.  A single
+ * pass, or a call while the target's stream is being captured, launches the kernels directly. */
 int sx_stream_iter(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double q, int iters);
 /* The same `iters` passes computed by one kernel that reads a once and writes a, b, c once;
  * bit-identical results (each element's chain of roundings is the same). */

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "sx.h"
 
@@ -120,11 +121,28 @@ struct sx_array {
     size_t data_bytes = 0;
 };
 
+// What the nodes of a captured run of STREAM passes bake in (zero-filled, compared bytewise).
+struct sx_pass_graph_key {
+    const void *a, *b, *c;
+    size_t n;
+    int dtype, passes;
+    uint64_t q_bits;
+    sx_launch_cfg cfg[4];  // copy, scale, add, triad
+};
+
 struct sx_executor {
     sx_target *t = nullptr;
     int policy = SX_PAR;
     bool fixed_cfg = false;
     sx_launch_cfg cfg{};
+    // sx_stream_iter's CUDA graphs (most recent last) and the private stream they are captured on
+    struct PassGraph {
+        sx_pass_graph_key key;
+        cudaGraphExec_t exec;
+    };
+    static constexpr size_t kMaxGraphs = 8;
+    std::vector<PassGraph> graphs;
+    cudaStream_t capture = nullptr;
 };
 
 struct sx_future {

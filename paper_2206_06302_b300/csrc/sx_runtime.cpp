@@ -429,6 +429,12 @@ int sx_executor_create(sx_target *t, sx_policy policy, const sx_launch_cfg *cfg,
 
 int sx_executor_destroy(sx_executor *e) {
     if (!e) return fail(SX_ERR_INVALID, "executor is NULL");
+    {
+        DeviceScope ds(e->t->device);
+        for (auto &g : e->graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (e->capture) cudaStreamDestroy(e->capture);
+    }
     delete e;
     return SX_OK;
 }
@@ -556,15 +562,97 @@ static int check_stream_arrays(sx_executor *e, sx_array *a, sx_array *b, sx_arra
     return SX_OK;
 }
 
+// One pass of Listing 4 (four launches in stream order) on stream `s`.
+static int enqueue_pass(sx_executor *e, cudaStream_t s, sx_array *a, sx_array *b, sx_array *c, double q,
+                        const sx_launch_cfg (&cfg)[4]) {
+    const int dt = a->dtype;
+    const size_t n = a->n;
+    SX_TRY(launch_stream_op(e->t, s, SX_OP_COPY, dt, a->ptr, nullptr, c->ptr, n, q, cfg[0]));  // c = a
+    SX_TRY(launch_stream_op(e->t, s, SX_OP_SCALE, dt, c->ptr, nullptr, b->ptr, n, q, cfg[1])); // b = c*q
+    SX_TRY(launch_stream_op(e->t, s, SX_OP_ADD, dt, a->ptr, b->ptr, c->ptr, n, q, cfg[2]));    // c = a+b
+    SX_TRY(launch_stream_op(e->t, s, SX_OP_TRIAD, dt, b->ptr, c->ptr, a->ptr, n, q, cfg[3]));  // a = b+c*q
+    return SX_OK;
+}
+
+// A graph of `key.passes` passes for this executor, captured on its private stream the first
+// time and kept (up to kMaxGraphs, oldest dropped).  Nothing is launched on failure; the caller
+// then launches directly, and the failure is kept too (a null entry), so it is not retried.
+static cudaGraphExec_t pass_graph(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double q,
+                                  const sx_pass_graph_key &key) {
+    for (size_t i = 0; i < e->graphs.size(); ++i) {
+        if (std::memcmp(&e->graphs[i].key, &key, sizeof key) == 0) {
+            auto g = e->graphs[i];
+            e->graphs.erase(e->graphs.begin() + i);
+            e->graphs.push_back(g);
+            return g.exec;
+        }
+    }
+    if (!e->capture && cudaStreamCreateWithFlags(&e->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        e->capture = nullptr;
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaStreamBeginCapture(e->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int rc = SX_OK;
+    for (int k = 0; k < key.passes && rc == SX_OK; ++k) rc = enqueue_pass(e, e->capture, a, b, c, q, key.cfg);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t end = cudaStreamEndCapture(e->capture, &graph);  // always ends the capture
+    cudaGraphExec_t exec = nullptr;
+    if (rc == SX_OK && end == cudaSuccess && graph &&
+        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        exec = nullptr;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (!exec) clear_error();
+    if (e->graphs.size() >= sx_executor::kMaxGraphs) {
+        if (e->graphs.front().exec) cudaGraphExecDestroy(e->graphs.front().exec);
+        e->graphs.erase(e->graphs.begin());
+    }
+    e->graphs.push_back({key, exec});
+    return exec;
+}
+
+// Passes run from CUDA graphs of up to kGraphPasses passes (4 kernel nodes each) when there
+// are at least two: one graph launch replaces up to 64 kernel launches, which dominate the
+// time of small arrays.  Same kernels in the same order, so the same bits.  Direct launches
+// are used for a single pass, while the target's stream is itself being captured, or if a
+// graph cannot be made.
+constexpr int kGraphPasses = 16;
+
 int sx_stream_iter(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double q, int iters) {
     SX_TRY(check_stream_arrays(e, a, b, c, iters));
     DeviceScope ds(e->t->device);
-    for (int k = 0; k < iters; ++k) {
-        SX_TRY(enqueue_op(e, SX_OP_COPY, a, nullptr, c, q));   // c = a
-        SX_TRY(enqueue_op(e, SX_OP_SCALE, c, nullptr, b, q));  // b = c*q
-        SX_TRY(enqueue_op(e, SX_OP_ADD, a, b, c, q));          // c = a+b
-        SX_TRY(enqueue_op(e, SX_OP_TRIAD, b, c, a, q));        // a = b+c*q
+    sx_launch_cfg cfg[4];
+    const int ops[4] = {SX_OP_COPY, SX_OP_SCALE, SX_OP_ADD, SX_OP_TRIAD};
+    for (int k = 0; k < 4; ++k) {
+        cfg[k] = resolve_cfg(e->t, ops[k], a->dtype, a->n, e->fixed_cfg ? &e->cfg : nullptr);
+        SX_TRY(validate_cfg(e->t, ops[k], cfg[k]));
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool graphs = iters >= 2 && a->n > 0 &&
+                        cudaStreamIsCapturing(e->t->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    int done = 0;
+    while (graphs && iters - done >= 2) {
+        sx_pass_graph_key key;
+        std::memset(&key, 0, sizeof key);
+        key.a = a->ptr;
+        key.b = b->ptr;
+        key.c = c->ptr;
+        key.n = a->n;
+        key.dtype = a->dtype;
+        key.passes = std::min(kGraphPasses, iters - done);
+        std::memcpy(&key.q_bits, &q, sizeof q);
+        std::memcpy(key.cfg, cfg, sizeof cfg);
+        cudaGraphExec_t g = pass_graph(e, a, b, c, q, key);
+        if (!g) break;
+        const int reps = (iters - done) / key.passes;
+        for (int r = 0; r < reps; ++r) SX_CUDA(cudaGraphLaunch(g, e->t->stream));
+        done += reps * key.passes;
+    }
+    for (; done < iters; ++done) SX_TRY(enqueue_pass(e, e->t->stream, a, b, c, q, cfg));
     return finish_call(e);
 }
 

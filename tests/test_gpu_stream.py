@@ -222,6 +222,73 @@ def test_stream_passes_match_oracle(target, executor, dt, fused):
         assert_bitwise(gc, c, f"c iters={iters}")
 
 
+@pytest.mark.parametrize("cfg", range(len(CFGS)))
+def test_stream_iter_graphs_match_oracle(target, cfg):
+    """Passes replayed from captured CUDA graphs (37 = 16 + 16 + 5 passes, then the same call
+    again from the executor's cache) give the oracle's bits for every launch shape, including the
+    TMA family, in both types."""
+    e = sx.sx_executor_create(target, sx.SX_PAR, CFGS[cfg])
+    try:
+        for dt, n in ((np.float64, 65536 + 7), (np.float32, 4099)):
+            a, b, c = si.stream_arrays(n, dt, base_seed=91)
+            da, db, dc = to_device(target, a), to_device(target, b), to_device(target, c)
+            for _ in range(2):
+                sx.sx_stream_iter(e, da, db, dc, 3.0, 37)
+                oracle.stream(a, b, c, 3.0, 37)
+                for got, want, nm in ((da, a, "a"), (db, b, "b"), (dc, c, "c")):
+                    assert_bitwise(to_host(got), want, f"{nm} {dt.__name__}")
+            for h in (da, db, dc):
+                sx.sx_free(h)
+    finally:
+        sx.sx_executor_destroy(e)
+
+
+def test_stream_iter_graph_cache_eviction(target):
+    """More array sets than the executor keeps graphs for, then the first set again."""
+    e = sx.sx_executor_create(target, sx.SX_PAR_TASK)
+    n = 3001
+    host = [si.stream_arrays(n, np.float64, base_seed=300 + k) for k in range(11)]
+    dev = [[to_device(target, h) for h in hs] for hs in host]
+    for k in list(range(11)) + [0, 1]:
+        sx.sx_stream_iter(e, *dev[k], 3.0, 3)
+        oracle.stream(*host[k], 3.0, 3)
+    sx.sx_executor_wait(e)
+    for k in range(11):
+        for got, want in zip(dev[k], host[k]):
+            assert_bitwise(to_host(got), want, f"set {k}")
+    for d in dev:
+        for h in d:
+            sx.sx_free(h)
+    sx.sx_executor_destroy(e)
+
+
+def test_stream_iter_inside_a_caller_capture():
+    """While the target's stream is being captured by the caller (torch.cuda.graph), the passes
+    are launched directly into that capture; replaying the caller's graph runs them."""
+    import torch
+    import paper_2206_06302_b300 as pkg
+    s = torch.cuda.Stream()
+    t = pkg.target_on_torch_stream(0, s)
+    e = sx.sx_executor_create(t, sx.SX_PAR_TASK)
+    n = 10007
+    a, b, c = si.stream_arrays(n, np.float64, base_seed=12)
+    da, db, dc = to_device(t, a), to_device(t, b), to_device(t, c)
+    sx.sx_target_synchronize(t)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sx.sx_stream_iter(e, da, db, dc, 3.0, 3)
+    for _ in range(2):
+        g.replay()
+        oracle.stream(a, b, c, 3.0, 3)
+    torch.cuda.synchronize()
+    for got, want in zip((da, db, dc), (a, b, c)):
+        assert_bitwise(to_host(got), want, "captured by the caller")
+    for h in (da, db, dc):
+        sx.sx_free(h)
+    sx.sx_executor_destroy(e)
+    sx.sx_target_destroy(t)
+
+
 def test_fused_equals_four_launches_unaligned(target, executor):
     import torch
     n = 50001
