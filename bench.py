@@ -675,8 +675,8 @@ def run_sweep(args):
     t = sx.target_on_torch_stream(0, stream)
     shapes = {
         "vector": dict(variant=sx.SX_VARIANT_VECTOR, threads=256, vec_bytes=32, unroll=2, fp64_mul=2),
-        "bulk": dict(variant=sx.SX_VARIANT_BULK, threads=512, blocks_per_sm=2, tile_bytes=16384,
-                     stages=3, fp64_mul=1),
+        "bulk": dict(variant=sx.SX_VARIANT_BULK, threads=256, blocks_per_sm=2, tile_bytes=16384,
+                     stages=3, fp64_mul=2),
     }
     execs = {k: sx.sx_executor_create(t, sx.SX_PAR_TASK, v) for k, v in shapes.items()}
     ops = (("copy", sx.SX_OP_COPY, 2), ("scale", sx.SX_OP_SCALE, 2), ("add", sx.SX_OP_ADD, 3),

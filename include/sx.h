@@ -79,13 +79,15 @@ typedef enum sx_op {
 typedef enum sx_policy { SX_PAR = 1, SX_PAR_TASK = 2 } sx_policy;
 
 /* Kernel family.  VECTOR: grid-stride loop of 16- or 32-byte vector loads/stores per thread.
- * BULK: a persistent kernel that stages tiles through shared memory with the Tensor Memory
- * Accelerator's bulk copies (cp.async.bulk global->shared, compute, shared->global).
+ * BULK: a persistent, warp-specialised kernel that stages input tiles through shared memory
+ * with the Tensor Memory Accelerator's bulk copies (a producer warp issues cp.async.bulk
+ * global->shared per pipeline stage; consumer warps compute from shared memory and store to
+ * global memory).
  * AUTO: the autotuner's choice for (op, dtype, size) if it has one, else a fixed default. */
 typedef enum sx_variant { SX_VARIANT_AUTO = 0, SX_VARIANT_VECTOR = 1, SX_VARIANT_BULK = 2 } sx_variant;
 
 /* Launch configuration of one algorithm call.  A zero field means "default".
- *   threads        threads per block (multiple of 32; VECTOR: 32..1024; BULK: 32..1024)
+ *   threads        threads per block (multiple of 32; VECTOR: 32..1024; BULK: 64..1024, one producer warp)
  *   blocks_per_sm  VECTOR: grid = SMs * blocks_per_sm with a grid-stride loop; 0 = one tile
  *                  per block (grid covers the array).  BULK: persistent blocks per SM (1..4)
  *   vec_bytes      VECTOR: 16 or 32 bytes per thread access

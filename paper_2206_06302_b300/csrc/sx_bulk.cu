@@ -1,18 +1,22 @@
-// sx_bulk.cu -- BULK family of the STREAM kernels: tiles staged through shared memory by the
-// Tensor Memory Accelerator's bulk copies (sm_90+ cp.async.bulk, no tensor map needed).
+// sx_bulk.cu -- BULK family of the STREAM kernels: input tiles staged through shared memory by
+// the Tensor Memory Accelerator's bulk copies (sm_90+ cp.async.bulk, no tensor map needed), with
+// warp-specialised blocks.
 //
-// One persistent block per SM (or two) walks its share of the tiles through a ring of `stages`
-// shared-memory slots.  Thread 0 is the producer: for each tile it arms the slot's mbarrier
-// with the expected byte count and issues one cp.async.bulk global->shared per input array.
-// All threads wait on the slot's mbarrier, apply the element operation in shared memory (in
-// place, in the first input's buffer), fence the generic-proxy writes for the async proxy, and
-// thread 0 writes the slot back with cp.async.bulk shared->global (a bulk async-group).  A slot
-// is refilled only once its store has finished reading it (cp.async.bulk.wait_group.read).
+// Persistent blocks (one or two per SM) walk their share of the tiles through a ring of `stages`
+// shared-memory slots, each with two mbarriers: `full` (armed by the producer with the slot's
+// byte count, completed by the bulk copies) and `empty` (one arrival per consumer warp).
+//   producer  lane 0 of warp 0: for each tile, wait until the slot is empty, arm `full`, issue
+//             one cp.async.bulk global->shared per input array;
+//   consumers the other warps: wait until the slot is full, read it (16-byte shared loads),
+//             apply the element operation and write the result straight to global memory with
+//             16-byte streaming stores, then each warp arrives on `empty`.
+// Loads of later tiles overlap the consumers' work on earlier ones, and a slot is free as soon as
+// it has been read (the stores leave from registers, so no bulk-store completion is awaited).
 //
-// Waits are bounded: each mbarrier wait gives up after ~2 s of %globaltimer, records a code in
-// the target's device error word, and the block leaves the loop together (the decision is
-// made with __syncthreads_or so no thread is left at a barrier); before leaving, thread 0 waits
-// (again bounded) for the loads it issued and for its stores.  Nothing traps.
+// Waits are bounded: a wait gives up after ~2 s of %globaltimer or as soon as another role has
+// given up (a shared abort flag), records a code in the target's device error word, and every
+// role leaves its loop; after the block's final barrier thread 0 waits (again bounded) for the
+// loads still in flight before shared memory is released.  Nothing traps.
 //
 // Alignment: every bulk copy starts on a 16-byte boundary and moves a multiple of 16 bytes.
 // Elements before the first 16-byte boundary and after the last whole 16 bytes are done one
@@ -74,24 +78,32 @@ __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint3
         : "memory");
 }
 
-__device__ __forceinline__ void bulk_store(void *dst, const void *src_smem, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
-                 "r"(smem_addr(src_smem)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Bounded wait that also gives up once *abort is set: true once the phase completed.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t phase, const volatile int *abort) {
+    if (mbar_try_wait(bar, phase)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int k = 0; k < 32; ++k)
+            if (mbar_try_wait(bar, phase)) return true;
+        if (*abort || global_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
 template <int OP, class T, int MM>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(1024, 1)
 k_stream_bulk(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t nbody,
               uint32_t tile_elems, int stages, T q, int *err) {
     constexpr bool HAS_Y = (OP == SX_OP_ADD || OP == SX_OP_TRIAD);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kMaxStages];
+    __shared__ __align__(8) uint64_t empty[kMaxStages];
+    __shared__ int abort_flag;
 
     // scalar edges: [0, head) and [head + nbody, n)
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,96 +117,104 @@ k_stream_bulk(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_
     const uint64_t ntiles = (nbody + tile_elems - 1) / tile_elems;
     const uint64_t nlocal = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     if (nlocal == 0) return;  // uniform across the block
-    if constexpr (OP == SX_OP_COPY) {
-        if (threadIdx.x != 0) return;  // a copy needs no compute: one thread drives the engine
-    }
 
     const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(T);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t consumer_warps = blockDim.x / 32 - 1;
     const T *xb = x + head;
     const T *yb = HAS_Y ? y + head : nullptr;
     T *ob = out + head;
     auto slot_x = [&](int s) { return smem + (size_t)s * (HAS_Y ? 2u : 1u) * tile_bytes; };
     auto slot_y = [&](int s) { return smem + (size_t)s * 2u * tile_bytes + tile_bytes; };
+    auto tile_start = [&](uint64_t j) { return (blockIdx.x + j * gridDim.x) * (uint64_t)tile_elems; };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], consumer_warps);
+        }
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
-    if constexpr (OP != SX_OP_COPY) __syncthreads();
+    __syncthreads();
+    volatile int *abort_v = &abort_flag;
 
     uint64_t issued = 0;  // producer only: tiles whose loads were issued
-    auto issue = [&](uint64_t j) {
-        const int s = (int)(j % (uint64_t)stages);
-        const uint64_t start = (blockIdx.x + j * gridDim.x) * (uint64_t)tile_elems;
-        const uint64_t cnt = min((uint64_t)tile_elems, nbody - start);
-        const uint32_t bytes = (uint32_t)(cnt * sizeof(T));
-        mbar_expect_tx(&full[s], HAS_Y ? 2 * bytes : bytes);
-        bulk_load(slot_x(s), xb + start, bytes, &full[s]);
-        if constexpr (HAS_Y) bulk_load(slot_y(s), yb + start, bytes, &full[s]);
-        issued = j + 1;
-    };
-    if (threadIdx.x == 0)
-        for (uint64_t j = 0; j < (uint64_t)stages && j < nlocal; ++j) issue(j);
-
-    bool aborted = false;
-    uint64_t j = 0;
-    for (; j < nlocal; ++j) {
-        const int s = (int)(j % (uint64_t)stages);
-        const uint32_t phase = (uint32_t)((j / (uint64_t)stages) & 1);
-        const bool ok = mbar_wait_bounded(&full[s], phase, kWaitLimitNs);
-        if constexpr (OP == SX_OP_COPY) {
-            if (!ok) {
-                aborted = true;
-                break;
-            }
-        } else {
-            if (__syncthreads_or(!ok)) {
-                aborted = true;
-                break;
-            }
-        }
-        const uint64_t start = (blockIdx.x + j * gridDim.x) * (uint64_t)tile_elems;
-        const uint64_t cnt = min((uint64_t)tile_elems, nbody - start);
-        const uint32_t bytes = (uint32_t)(cnt * sizeof(T));
-        if constexpr (OP != SX_OP_COPY) {
-            uint64_t *px = reinterpret_cast<uint64_t *>(slot_x(s));
-            const uint64_t *py = HAS_Y ? reinterpret_cast<const uint64_t *>(slot_y(s)) : nullptr;
-            const uint32_t nv = bytes / 16;
-            for (uint32_t v = threadIdx.x; v < nv; v += blockDim.x) {
-                uint64_t a0, a1, b0 = 0, b1 = 0;
-                asm volatile("ld.shared.v2.u64 {%0,%1}, [%2];" : "=l"(a0), "=l"(a1) : "r"(smem_addr(px + 2 * v)));
-                if constexpr (HAS_Y)
-                    asm volatile("ld.shared.v2.u64 {%0,%1}, [%2];" : "=l"(b0), "=l"(b1) : "r"(smem_addr(py + 2 * v)));
-                const uint64_t r0 = op_word<OP, T, MM>(a0, b0, q, 0), r1 = op_word<OP, T, MM>(a1, b1, q, 1);
-                asm volatile("st.shared.v2.u64 [%0], {%1,%2};" ::"r"(smem_addr(px + 2 * v)), "l"(r0), "l"(r1)
-                             : "memory");
-            }
-            fence_async_smem();
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            bulk_store(ob + start, slot_x(s), bytes);
-            bulk_commit();
-            if (j >= 1 && j - 1 + (uint64_t)stages < nlocal) {
-                bulk_wait_read_1();  // the store of tile j-1 has read its slot
-                issue(j - 1 + (uint64_t)stages);
-            }
-        }
-    }
-    if (threadIdx.x == 0) {
-        if (aborted) {
-            atomicExch(err, kErrBulkWait);
-            // wait, bounded, for the loads still in flight before shared memory is released
-            for (uint64_t k = j; k < issued; ++k) {
-                const int s = (int)(k % (uint64_t)stages);
-                if (!mbar_wait_bounded(&full[s], (uint32_t)((k / (uint64_t)stages) & 1), kWaitLimitNs)) {
-                    atomicExch(err, kErrBulkDrain);
+    if (warp == 0) {
+        if (lane == 0) {
+            for (uint64_t j = 0; j < nlocal; ++j) {
+                const int s = (int)(j % (uint64_t)stages);
+                if (j >= (uint64_t)stages &&
+                    !mbar_wait_or_abort(&empty[s], (uint32_t)((j / (uint64_t)stages - 1) & 1), abort_v)) {
+                    *abort_v = 1;
                     break;
                 }
+                const uint64_t start = tile_start(j);
+                const uint32_t bytes = (uint32_t)(min((uint64_t)tile_elems, nbody - start) * sizeof(T));
+                mbar_expect_tx(&full[s], HAS_Y ? 2 * bytes : bytes);
+                bulk_load(slot_x(s), xb + start, bytes, &full[s]);
+                if constexpr (HAS_Y) bulk_load(slot_y(s), yb + start, bytes, &full[s]);
+                issued = j + 1;
             }
         }
-        bulk_wait_all();
+    } else {
+        const uint32_t ctid = threadIdx.x - 32, ncons = blockDim.x - 32;
+        for (uint64_t j = 0; j < nlocal; ++j) {
+            const int s = (int)(j % (uint64_t)stages);
+            if (!mbar_wait_or_abort(&full[s], (uint32_t)((j / (uint64_t)stages) & 1), abort_v)) {
+                *abort_v = 1;
+                break;
+            }
+            const uint64_t start = tile_start(j);
+            const uint32_t nv = (uint32_t)(min((uint64_t)tile_elems, nbody - start) * sizeof(T) / 16);
+            const uint32_t sx0 = smem_addr(slot_x(s));
+            const uint32_t sy0 = HAS_Y ? smem_addr(slot_y(s)) : 0u;
+            char *og = reinterpret_cast<char *>(ob + start);
+            // two 16-byte vectors per thread and step; a lone last vector on its own (no work
+            // on words that are not there)
+            auto vec = [&](uint32_t v, uint64_t (&r)[2]) {
+                uint64_t a0, a1, b0 = 0, b1 = 0;
+                asm volatile("ld.shared.v2.u64 {%0,%1}, [%2];" : "=l"(a0), "=l"(a1) : "r"(sx0 + 16 * v));
+                if constexpr (HAS_Y)
+                    asm volatile("ld.shared.v2.u64 {%0,%1}, [%2];" : "=l"(b0), "=l"(b1) : "r"(sy0 + 16 * v));
+                r[0] = op_word<OP, T, MM>(a0, b0, q, 0);
+                r[1] = op_word<OP, T, MM>(a1, b1, q, 1);
+            };
+            auto put = [&](uint32_t v, const uint64_t (&r)[2]) {
+                asm volatile("st.global.cs.v2.u64 [%0], {%1,%2};" ::"l"(og + 16 * (uint64_t)v), "l"(r[0]), "l"(r[1])
+                             : "memory");
+            };
+            uint32_t v = ctid;
+            for (; v + ncons < nv; v += 2 * ncons) {
+                uint64_t r0[2], r1[2];
+                vec(v, r0);
+                vec(v + ncons, r1);
+                put(v, r0);
+                put(v + ncons, r1);
+            }
+            if (v < nv) {
+                uint64_t r0[2];
+                vec(v, r0);
+                put(v, r0);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // this warp has read the slot
+        }
+    }
+    __syncthreads();  // every role has left its loop (all waits above are bounded)
+    if (threadIdx.x == 0 && *abort_v) {
+        atomicExch(err, kErrBulkWait);
+        // the most recent load into each slot, if any is still in flight, lands before the
+        // block's shared memory is released
+        const uint64_t first = issued > (uint64_t)stages ? issued - (uint64_t)stages : 0;
+        for (uint64_t k = first; k < issued; ++k) {
+            const int s = (int)(k % (uint64_t)stages);
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((k / (uint64_t)stages) & 1), kWaitLimitNs)) {
+                atomicExch(err, kErrBulkDrain);
+                break;
+            }
+        }
     }
 }
 
@@ -266,8 +286,9 @@ int dispatch_bulk(const sx_target *t, cudaStream_t s, int op, const void *x, con
 }  // namespace
 
 int validate_bulk_cfg(const sx_target *t, int op, const sx_launch_cfg &c) {
-    if (c.threads < 32 || c.threads > 1024 || c.threads % 32)
-        return fail(SX_ERR_INVALID, "BULK threads=%d: need a multiple of 32 in [32, 1024]", c.threads);
+    if (c.threads < 64 || c.threads > 1024 || c.threads % 32)
+        return fail(SX_ERR_INVALID, "BULK threads=%d: need a multiple of 32 in [64, 1024] (a producer warp "
+                    "and at least one consumer warp)", c.threads);
     if (c.tile_bytes < 1024 || c.tile_bytes > 65536 || c.tile_bytes % 1024)
         return fail(SX_ERR_INVALID, "BULK tile_bytes=%d: need a multiple of 1024 in [1024, 65536]", c.tile_bytes);
     if (c.stages < 2 || c.stages > kMaxStages)

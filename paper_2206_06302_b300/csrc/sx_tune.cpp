@@ -209,10 +209,10 @@ static std::vector<sx_launch_cfg> vector_pass2(const sx_launch_cfg &best) {
 
 static std::vector<sx_launch_cfg> bulk_candidates(int op, int dtype) {
     std::vector<sx_launch_cfg> v;
-    const int mm = mul64(op, dtype) ? 1 : 0;
+    const int mm = mul64(op, dtype) ? 2 : 0;  // half of the FP64 products on the integer units
     for (int tile : {8192, 16384, 32768})
-        for (int st : {3, 4, 6})
-            for (int th : {256, 512, 1024})
+        for (int st : {2, 3, 4, 6})
+            for (int th : {128, 256, 512, 1024})
                 for (int bps : {1, 2}) {
                     sx_launch_cfg c{};
                     c.variant = SX_VARIANT_BULK;
