@@ -335,7 +335,9 @@ int sx_tune(sx_target *t, sx_op op, sx_dtype dtype, size_t n, sx_launch_cfg *bes
  * items (outputs are overwritten), store it for batches with a similar item mix, rebuild `b`
  * with it and return it.  *ms = device time of one launch with the best shape. */
 int sx_tune_batch(sx_batch *b, sx_batch_cfg *best, float *ms);
-/* Look up the table: SX_OK and *cfg if an entry covers (op, dtype, n), else SX_ERR_NOT_READY. */
+/* Look up the table: SX_OK and *cfg = the entry of the nearest tuned log2(n) bucket for
+ * (this target's device, op, dtype), the larger bucket on a tie; SX_ERR_NOT_READY if none.
+ * Executors whose launch configuration leaves the variant at AUTO use the same lookup. */
 int sx_tune_lookup(const sx_target *t, sx_op op, sx_dtype dtype, size_t n, sx_launch_cfg *cfg);
 /* Persist / restore the table as JSON (entries for other devices are kept as they are). */
 int sx_tune_save(const char *path);

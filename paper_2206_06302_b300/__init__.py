@@ -5,14 +5,34 @@ The compute path is ``libsx.so`` (CUDA for sm_103a, C ABI in ``include/sx.h``); 
 ctypes binding with the header's names.  This module adds two torch conveniences: a target
 that enqueues on a torch stream, and wrapping a CUDA tensor's storage as a borrowed array.
 Importing fails loudly if the library has not been built.
+
+On import the tuner table shipped with the package (``tune_b300.json``: launch shapes measured
+on B300 for the four kernels, both types, array sizes 2^16..2^29) is loaded, so executors that
+leave the variant at AUTO use it; entries for other devices are ignored by the lookup.
 """
 from __future__ import annotations
+
+import os
 
 from . import sx
 from .sx import *  # noqa: F401,F403  (the header's names)
 
 __all__ = [n for n in dir(sx) if n.startswith(("sx_", "SX_"))] + [
-    "sx", "SxError", "target_on_torch_stream", "wrap_tensor", "dtype_of"]
+    "sx", "SxError", "target_on_torch_stream", "wrap_tensor", "dtype_of", "SHIPPED_TUNE_TABLE",
+    "load_shipped_tune_table"]
+
+SHIPPED_TUNE_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_b300.json")
+
+
+def load_shipped_tune_table() -> bool:
+    """Load the shipped tuner table into the library's table (True if it exists)."""
+    if os.path.exists(SHIPPED_TUNE_TABLE):
+        sx.sx_tune_load(SHIPPED_TUNE_TABLE)
+        return True
+    return False
+
+
+load_shipped_tune_table()
 
 
 def dtype_of(tensor) -> int:

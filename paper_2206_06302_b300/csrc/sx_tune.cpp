@@ -147,12 +147,21 @@ int time_launches(cudaStream_t s, F &&launch, int warm, int reps, int trials, fl
 
 }  // namespace
 
+// The entry of the nearest tuned log2(n) bucket for (device, op, dtype); on a tie the larger.
 bool tune_table_lookup(const sx_target *t, int op, int dtype, size_t n, sx_launch_cfg *cfg) {
     std::lock_guard<std::mutex> g(g_mu);
     if (g_ops.empty()) return false;
-    auto it = g_ops.find(OpKey{t->name, op, dtype, log2_bucket((double)n)});
-    if (it == g_ops.end()) return false;
-    *cfg = it->second;
+    const int b = log2_bucket((double)n);
+    auto same = [&](const std::map<OpKey, sx_launch_cfg>::const_iterator &i) {
+        return i != g_ops.end() && i->first.dev == t->name && i->first.op == op && i->first.dtype == dtype;
+    };
+    auto hi = g_ops.lower_bound(OpKey{t->name, op, dtype, b});  // first bucket >= b
+    auto lo = hi;
+    const bool has_lo = hi != g_ops.begin() && same(--lo);
+    const bool has_hi = same(hi);
+    if (!has_lo && !has_hi) return false;
+    const bool take_hi = has_hi && (!has_lo || hi->first.bucket - b <= b - lo->first.bucket);
+    *cfg = take_hi ? hi->second : lo->second;
     return true;
 }
 

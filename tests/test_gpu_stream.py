@@ -598,3 +598,41 @@ def test_passes_on_several_targets_at_once():
         sx.sx_executor_destroy(e)
     for t in tgts:
         sx.sx_target_destroy(t)
+
+
+def test_tuner_lookup_takes_the_nearest_bucket(tmp_path):
+    """A table with triad FP64 entries at log2 buckets 20 and 24 only: sizes in between take the
+    nearer entry (the larger on a tie), sizes outside take the closest end, other ops none; an
+    AUTO executor launches with the looked-up shape and stays exact."""
+    import json
+    t = sx.sx_target_create(0)
+    name = sx.sx_target_info_get(t)["name"]
+
+    def entry(bucket, threads):
+        return {"device": name, "op": sx.SX_OP_TRIAD, "dtype": sx.SX_F64, "bucket": bucket, "variant": 1,
+                "threads": threads, "blocks_per_sm": 0, "vec_bytes": 16, "unroll": 1, "cache_hint": 0,
+                "tile_bytes": 0, "stages": 0, "fp64_mul": 2}
+    path = tmp_path / "table.json"
+    path.write_text(json.dumps({"ops": [entry(20, 128), entry(24, 512)], "batch": []}))
+    sx.sx_tune_clear()
+    try:
+        sx.sx_tune_load(str(path))
+        for n, threads in ((1 << 10, 128), (1 << 20, 128), (1 << 21, 128), (1 << 22, 512), (1 << 23, 512),
+                           (1 << 30, 512)):
+            assert sx.sx_tune_lookup(t, sx.SX_OP_TRIAD, sx.SX_F64, n)["threads"] == threads, n
+        assert sx.sx_tune_lookup(t, sx.SX_OP_ADD, sx.SX_F64, 1 << 20) is None
+        assert sx.sx_tune_lookup(t, sx.SX_OP_TRIAD, sx.SX_F32, 1 << 20) is None
+        e = sx.sx_executor_create(t, sx.SX_PAR)
+        assert sx.sx_executor_resolve(e, sx.SX_OP_TRIAD, sx.SX_F64, 3 << 20)["threads"] == 128  # bucket 21
+        assert sx.sx_executor_resolve(e, sx.SX_OP_TRIAD, sx.SX_F64, 3 << 21)["threads"] == 512  # 22: a tie
+        x, y = _inputs(3 << 21, np.float64, 13)
+        dx, dy, do = to_device(t, x), to_device(t, y), empty(t, np.float64, x.size)
+        sx.sx_execute(e, sx.SX_OP_TRIAD, dx, dy, do, 3.0)
+        assert_bitwise(to_host(do), oracle.triad(x, y, 3.0), "auto from the table")
+        for h in (dx, dy, do):
+            sx.sx_free(h)
+        sx.sx_executor_destroy(e)
+    finally:
+        sx.sx_tune_clear()
+        sx.load_shipped_tune_table()
+        sx.sx_target_destroy(t)
