@@ -432,9 +432,12 @@ int sx_server_replay(sx_server *s, const sx_request *reqs, const double *t_arriv
 int sx_server_poll(sx_server *s, uint64_t id, sx_request_status *st);
 /* Wait until the request is DONE or REJECTED (SX_ERR_TIMEOUT after timeout_ms >= 0). */
 int sx_server_wait(sx_server *s, uint64_t id, int64_t timeout_ms, sx_request_status *st);
-/* Copy n elements of a DONE request's array (0 = x, 1 = y, 2 = out) to host memory. */
+/* Copy n elements of a DONE request's array (0 = x, 1 = y, 2 = out) to host memory; returns
+ * once the copy is complete.  Reads from several threads may run at once. */
 int sx_server_read(sx_server *s, uint64_t id, int which, void *host, size_t n);
-/* Free a DONE (or REJECTED) request's arena memory. */
+/* Free a DONE (or REJECTED) request's arena memory.  The request is RELEASED at once (later
+ * reads fail); if reads of it are in progress on other threads, the memory is freed when the
+ * last of them ends. */
 int sx_server_release(sx_server *s, uint64_t id);
 int sx_server_stats_get(sx_server *s, sx_server_stats *st);
 /* Finish all admitted work, reject what is still queued, stop the thread, free the arena. */

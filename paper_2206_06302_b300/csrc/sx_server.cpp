@@ -22,7 +22,10 @@
 // launches (construct x, construct y, operation) in arrival order, like a client calling the
 // algorithms directly.
 //
-// All waits are on the host (event queries, condition variables); no kernel waits on another.
+// The host waits by polling (the step completion word, FIFO events) and on condition variables.
+// On the device a step waits for its predecessor only through programmatic dependent launch
+// (griddepcontrol.wait, a dependency the hardware resolves when the previous kernel in the
+// stream completes); no kernel spins on memory another kernel writes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -111,6 +114,8 @@ struct Request {
     int bypassed = 0;         // admission: times a later request was admitted first
     uint64_t admit_seq = 0;   // order of admission
     uint64_t inputs_step = 0; // step that holds the last piece of the inputs construction
+    int readers = 0;          // sx_server_read copies in progress from the request's arrays
+    bool free_deferred = false;  // released while being read: the last reader frees the arrays
 };
 
 bool has_y(int op) { return op == SX_OP_ADD || op == SX_OP_TRIAD; }
@@ -846,19 +851,37 @@ int sx_server_read(sx_server *s, uint64_t id, int which, void *host, size_t n) {
     if (which < 0 || which > 2) return fail(SX_ERR_INVALID, "which=%d: 0 = x, 1 = y, 2 = out", which);
     const void *src;
     size_t bytes;
+    Request *q;
     {
         ApiLock g(s);
-        Request *q = find(s, id);
+        q = find(s, id);
         if (!q) return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
         if (q->state != SX_REQ_DONE || !q->allocated) return fail(SX_ERR_STATE, "request %llu has no resident result", (unsigned long long)id);
         if (!q->bytes[which]) return fail(SX_ERR_INVALID, "request %llu has no array %d", (unsigned long long)id, which);
         if (n > q->r.n) return fail(SX_ERR_INVALID, "n=%zu exceeds the request length", n);
         src = ptr_of(s, q, which);
         bytes = n * dtype_size(q->r.dtype);
+        q->readers++;  // the arrays stay allocated until the copy is done (see sx_server_release)
     }
-    DeviceScope ds(s->t->device);
-    SX_CUDA(cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, s->read_stream));
-    SX_CUDA(cudaStreamSynchronize(s->read_stream));
+    cudaError_t e;
+    {
+        DeviceScope ds(s->t->device);
+        e = cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, s->read_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->read_stream);
+    }
+    bool freed = false;
+    {
+        ApiLock g(s);
+        if (--q->readers == 0 && q->free_deferred) {
+            q->free_deferred = false;
+            release_arrays(s, q);
+            s->admit_dirty = true;
+            s->arrivals.fetch_add(1, std::memory_order_release);
+            freed = true;
+        }
+    }
+    if (freed) s->cv.notify_one();
+    if (e != cudaSuccess) return cuda_fail(e, "server read");
     return SX_OK;
 }
 
@@ -870,10 +893,14 @@ int sx_server_release(sx_server *s, uint64_t id) {
         if (!q) return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
         if (q->state != SX_REQ_DONE && q->state != SX_REQ_REJECTED)
             return fail(SX_ERR_STATE, "request %llu is not finished", (unsigned long long)id);
+        if (q->state == SX_REQ_DONE) q->state = SX_REQ_RELEASED;  // no new reads from here on
+        if (q->readers > 0) {
+            q->free_deferred = true;  // a read in progress frees the arrays when it ends
+            return SX_OK;
+        }
         release_arrays(s, q);
         s->admit_dirty = true;
         s->arrivals.fetch_add(1, std::memory_order_release);
-        if (q->state == SX_REQ_DONE) q->state = SX_REQ_RELEASED;
     }
     s->cv.notify_one();  // memory freed: admission may proceed
     return SX_OK;

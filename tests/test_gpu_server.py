@@ -193,3 +193,38 @@ def test_served_full_size_requests(target):
             assert np.array_equal(out.view(np.uint8), want.view(np.uint8)), (rid, r["op"], n)
         sx.sx_server_release(s, rid)
     sx.sx_server_destroy(s)
+
+
+def test_release_during_a_read_waits_for_the_read(target):
+    """A request is released (and a second request that can only fit in the same memory is
+    submitted) while another thread is still copying the first one's output to the host: the
+    copy sees the first result intact, the second request is admitted only after the copy, and
+    a read after the release is refused."""
+    import threading
+    import time
+    n = 1 << 25
+    a = dict(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=n, q=3.0, seed_x=11, seed_y=12, lo=-1.0, hi=1.0)
+    b = dict(a, seed_x=21, seed_y=22)
+    s = sx.sx_server_create(target, budget_bytes=3 * 8 * n + (1 << 20))
+    try:
+        ra = sx.sx_server_submit(s, **a)
+        assert sx.sx_server_wait(s, ra, 60000)["state"] == sx.SX_REQ_DONE
+        got = np.empty(n, np.float64)
+        reads = []
+        th = threading.Thread(target=lambda: reads.append(
+            sx.sx_server_read(s, ra, 2, got.ctypes.data, n)))
+        th.start()
+        time.sleep(0.002)
+        sx.sx_server_release(s, ra)
+        rb = sx.sx_server_submit(s, **b)
+        th.join()
+        with pytest.raises(sx.SxError) as ei:
+            sx.sx_server_read(s, ra, 2, got.ctypes.data, 1)
+        assert ei.value.status == sx.SX_ERR_STATE
+        assert np.array_equal(got.view(np.uint64), _expected(a)[2].view(np.uint64))
+        st = sx.sx_server_wait(s, rb, 60000)
+        assert st["state"] == sx.SX_REQ_DONE
+        assert np.array_equal(_read(s, rb, 2, b).view(np.uint64), _expected(b)[2].view(np.uint64))
+        sx.sx_server_release(s, rb)
+    finally:
+        sx.sx_server_destroy(s)
