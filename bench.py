@@ -447,7 +447,7 @@ def fused_section(sx, torch, t, stream, n, rank, passes=100):
             "fused_dram_bytes": 4 * n * 8, "bit_identical": same}
 
 
-def small_n_section(sx, torch, passes=100, sizes=(1 << 10, 1 << 14, 1 << 16, 1 << 18, 1 << 20, 1 << 22)):
+def small_n_section(sx, torch, device=0, passes=100, sizes=(1 << 10, 1 << 14, 1 << 16, 1 << 18, 1 << 20, 1 << 22)):
     """Small arrays, where a STREAM pass is bound by the cost of its four kernel launches (the
     paper's small-size overhead): `passes` passes as `passes` single-pass calls (direct
     launches), as one sx_stream_iter call (replayed from CUDA graphs), and fused into one kernel.
@@ -455,7 +455,7 @@ def small_n_section(sx, torch, passes=100, sizes=(1 << 10, 1 << 14, 1 << 16, 1 <
     graph is captured by an untimed warm-up call); FP64; results checked against the oracle."""
     import oracle
     import stream_inputs as si
-    tt = sx.sx_target_create(0)
+    tt = sx.sx_target_create(device)
     e = sx.sx_executor_create(tt, sx.SX_PAR_TASK)
     rows = []
     for n in sizes:
@@ -504,7 +504,7 @@ def small_n_section(sx, torch, passes=100, sizes=(1 << 10, 1 << 14, 1 << 16, 1 <
             "runs": rows}
 
 
-def overlap_section(sx, torch, sets=4, passes=20, sizes=(1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24)):
+def overlap_section(sx, torch, device=0, sets=4, passes=20, sizes=(1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24)):
     """Asynchronous execution over several targets (Section 3.3 async_execute/bulk_async_execute,
     Section 4.2: a target is a device and a stream).  `sets` independent FP64 STREAM array sets,
     `passes` passes each, enqueued pass by pass with PAR_TASK executors and waited for at the end:
@@ -514,7 +514,7 @@ def overlap_section(sx, torch, sets=4, passes=20, sizes=(1 << 16, 1 << 18, 1 << 
     results checked against the oracle (all elements up to 2^20, the first 4096 above)."""
     import oracle
     import stream_inputs as si
-    tgts = [sx.sx_target_create(0) for _ in range(sets)]
+    tgts = [sx.sx_target_create(device) for _ in range(sets)]
     execs = [sx.sx_executor_create(tt, sx.SX_PAR_TASK) for tt in tgts]
     rows = []
     for n in sizes:
@@ -576,12 +576,12 @@ def overlap_section(sx, torch, sets=4, passes=20, sizes=(1 << 16, 1 << 18, 1 << 
             "runs": rows}
 
 
-def copies_section(sx, torch, t, sizes=(1 << 20, 1 << 24, 1 << 28, 1 << 30), reps=5):
+def copies_section(sx, torch, t, device=0, sizes=(1 << 20, 1 << 24, 1 << 28, 1 << 30), reps=5):
     """Host<->device copy algorithm (Section 4.2: copy between host and device is a CUDA memcpy)
     through sx_copy_h2d / sx_copy_d2h on pinned and pageable host buffers, and both directions at
     once (pinned; the two copies on two targets' streams).  Best of `reps`, host clock."""
     rows = []
-    t2 = sx.sx_target_create(0)
+    t2 = sx.sx_target_create(device)
     for nbytes in sizes:
         d1, d2 = sx.sx_alloc(t, sx.SX_U8, nbytes), sx.sx_alloc(t2, sx.SX_U8, nbytes)
         pin1 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
@@ -849,11 +849,11 @@ def run_ours(args):
     if not args.quick:
         extra["fused_100_passes"] = fused_section(sx, torch, t, stream, n, rank)
     if not args.quick and "small" in args.sections:
-        extra["small_n_passes"] = small_n_section(sx, torch)
+        extra["small_n_passes"] = small_n_section(sx, torch, local)
     if not args.quick and "overlap" in args.sections:
-        extra["overlap_targets"] = overlap_section(sx, torch)
+        extra["overlap_targets"] = overlap_section(sx, torch, local)
     if not args.quick and "copies" in args.sections:
-        extra["copies"] = copies_section(sx, torch, t)
+        extra["copies"] = copies_section(sx, torch, t, local)
 
     # ---- CPU oracle on a bounded sample (rank 0, N=1 only) ------------------------------------
     cpu = None
