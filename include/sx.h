@@ -166,7 +166,7 @@ int sx_alloc(sx_target *t, sx_dtype dtype, size_t n, sx_array **out);
 /* Borrow n elements of device memory at `device_ptr` (e.g. a torch tensor's storage).  Not
  * charged to the budget, never freed.  Any alignment of the element type is accepted. */
 int sx_array_wrap(sx_target *t, sx_dtype dtype, void *device_ptr, size_t n, sx_array **out);
-/* Release an array (bulk_destroy is a no-op for these trivially destructible types). */
+/* Release an array and, for owned arrays, its device memory. */
 int sx_free(sx_array *a);
 int sx_array_data(const sx_array *a, void **device_ptr, size_t *n, int *dtype);
 /* Owned arrays: *ok = 1 if the 256 guard bytes past the last element are untouched.  Waits
@@ -180,6 +180,12 @@ int sx_bulk_construct(sx_array *a, double value);
  * of SplitMix64 (Steele, Lea & Flood 2014; Vigna's 64-bit finaliser) started from state
  * `seed`.  Enqueued on the target stream. */
 int sx_seed_uniform(sx_array *a, uint64_t seed, double lo, double hi);
+/* bulk_destroy (Section 3.2, Listing 1: ends the lifetime of the array's elements on its
+ * target, never fails for a valid array).  The element types here are trivially destructible,
+ * so nothing runs on the device and no memory is freed (sx_free does that); the call exists so
+ * that code written against the allocator interface pairs each bulk construction with its
+ * destruction.  SX_ERR_INVALID only for a NULL array. */
+int sx_bulk_destroy(sx_array *a);
 
 /* ---- host<->device copy: Section 4.2 (copy specialised to CUDA memcpy) ---------------- */
 /* Copy n elements between host memory and the array, starting at element 0.  The blocking

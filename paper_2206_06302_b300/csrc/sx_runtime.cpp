@@ -374,6 +374,11 @@ int sx_bulk_construct(sx_array *a, double value) {
     return launch_fill(a->t->stream, a->dtype, a->ptr, a->n, value);
 }
 
+int sx_bulk_destroy(sx_array *a) {
+    if (!a) return fail(SX_ERR_INVALID, "array is NULL");
+    return SX_OK;  // trivially destructible elements: no destructor to run
+}
+
 int sx_seed_uniform(sx_array *a, uint64_t seed, double lo, double hi) {
     if (!a) return fail(SX_ERR_INVALID, "array is NULL");
     DeviceScope ds(a->t->device);

@@ -123,6 +123,7 @@ _PROTOS = {
     "sx_array_data": [P, PP, C.POINTER(C.c_size_t), C.POINTER(C.c_int)],
     "sx_array_guard_ok": [P, C.POINTER(C.c_int)],
     "sx_bulk_construct": [P, D],
+    "sx_bulk_destroy": [P],
     "sx_seed_uniform": [P, U64, D, D],
     "sx_copy_h2d": [P, P, SZ],
     "sx_copy_d2h": [P, P, SZ],
@@ -295,6 +296,10 @@ def sx_array_guard_ok(a) -> bool:
 
 def sx_bulk_construct(a, value: float) -> None:
     _check(lib.sx_bulk_construct(a, value), "sx_bulk_construct")
+
+
+def sx_bulk_destroy(a) -> None:
+    _check(lib.sx_bulk_destroy(a), "sx_bulk_destroy")
 
 
 def sx_seed_uniform(a, seed: int, lo: float = -1.0, hi: float = 1.0) -> None:

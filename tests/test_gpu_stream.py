@@ -395,7 +395,12 @@ def test_bulk_construct_fill(target):
         d = empty(target, dt, 1001)
         sx.sx_bulk_construct(d, 2.0)
         assert np.all(to_host(d) == 2)
+        sx.sx_bulk_destroy(d)  # Listing 1's pair to bulk_construct; frees nothing
+        assert sx.sx_array_data(d)[1] == 1001
         sx.sx_free(d)
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_bulk_destroy(None)
+    assert ei.value.status == sx.SX_ERR_INVALID
 
 
 def test_to_upper_listing3(target, executor):
