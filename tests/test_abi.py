@@ -92,3 +92,25 @@ def test_no_device_means_no_target():
     import paper_2206_06302_b300 as p
     with pytest.raises(p.SxError):
         p.sx_target_create(0)
+
+
+def build_c_client(tmp_path):
+    """Compile and link tests/c_abi_program.c, a plain C11 client, against libsx."""
+    lib = _builder().build()
+    exe = str(tmp_path / "c_abi_program")
+    cmd = ["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "c_abi_program.c"), "-o", exe, "-L", os.path.dirname(lib), "-lsx",
+           "-Wl,-rpath," + os.path.dirname(lib)]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    return exe
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """sx.h compiles as strict C11 and a C client links against libsx; without a device it
+    reports that and exits 2 (no compute call is made)."""
+    import torch
+    exe = build_c_client(tmp_path)
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the GPU test runs the client")
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 2 and "no device" in r.stderr, (r.returncode, r.stderr)

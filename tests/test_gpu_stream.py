@@ -641,3 +641,11 @@ def test_tuner_lookup_takes_the_nearest_bucket(tmp_path):
         sx.sx_tune_clear()
         sx.load_shipped_tune_table()
         sx.sx_target_destroy(t)
+
+
+def test_c_client_closed_form(tmp_path):
+    """A plain C11 program (tests/c_abi_program.c) runs STREAM's closed form through the C ABI."""
+    import subprocess
+    from test_abi import build_c_client
+    r = subprocess.run([build_c_client(tmp_path)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "closed form ok" in r.stdout, (r.returncode, r.stdout, r.stderr)
