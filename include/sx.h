@@ -139,7 +139,8 @@ int sx_target_count(int *count);
 int sx_target_create(int device, sx_target **out);
 /* A target that borrows `stream` (a cudaStream_t; NULL = create an owned stream) and caps
  * allocation through it at `budget_bytes` (0 = total device memory).  The stream must
- * outlive the target. */
+ * outlive the target.  To borrow the legacy default stream (the one other libraries use when
+ * they name stream 0), pass its handle cudaStreamLegacy, (void *)0x1. */
 int sx_target_create_ext(int device, void *stream, size_t budget_bytes, sx_target **out);
 int sx_target_destroy(sx_target *t);
 int sx_target_info_get(const sx_target *t, sx_target_info *out);

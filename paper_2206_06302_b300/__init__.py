@@ -43,12 +43,17 @@ def dtype_of(tensor) -> int:
     return m[tensor.dtype]
 
 
+CUDA_STREAM_LEGACY = 0x1  # the runtime's handle of the legacy default stream (cudaStreamLegacy)
+
+
 def target_on_torch_stream(device: int = 0, stream=None, budget_bytes: int = 0):
-    """A target on ``device`` that enqueues on ``stream`` (default: torch's current stream)."""
+    """A target on ``device`` that enqueues on ``stream`` (default: torch's current stream), so
+    that its work is ordered with torch's on that stream.  torch names the legacy default
+    stream 0, which the C ABI reads as "create a stream": it is passed as cudaStreamLegacy."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream(device)
-    return sx.sx_target_create_ext(device, stream.cuda_stream, budget_bytes)
+    return sx.sx_target_create_ext(device, stream.cuda_stream or CUDA_STREAM_LEGACY, budget_bytes)
 
 
 def wrap_tensor(target, tensor):

@@ -649,3 +649,32 @@ def test_c_client_closed_form(tmp_path):
     from test_abi import build_c_client
     r = subprocess.run([build_c_client(tmp_path)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "closed form ok" in r.stdout, (r.returncode, r.stdout, r.stderr)
+
+
+def test_target_on_torchs_default_stream_is_ordered_with_torch():
+    """torch names its default (legacy) stream 0; the target borrows it as cudaStreamLegacy, so
+    a library call enqueued after an asynchronous torch copy reads the copied data, and torch
+    reads the library's result after it."""
+    import torch
+    import paper_2206_06302_b300 as pkg
+    assert torch.cuda.current_stream().cuda_stream == 0
+    t = pkg.target_on_torch_stream(0)
+    assert sx.sx_target_stream(t) == pkg.CUDA_STREAM_LEGACY
+    e = sx.sx_executor_create(t, sx.SX_PAR_TASK)
+    n = 1 << 26
+    hx = torch.from_numpy(si.uniform(77, n, np.float64)).pin_memory()
+    hy = torch.from_numpy(si.uniform(78, n, np.float64)).pin_memory()
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    o = torch.zeros_like(x)
+    torch.cuda.synchronize()
+    x.copy_(hx, non_blocking=True)  # ~10 ms of copies still in flight when the triad is enqueued
+    y.copy_(hy, non_blocking=True)
+    wx, wy, wo = (pkg.wrap_tensor(t, v) for v in (x, y, o))
+    sx.sx_execute_async(e, sx.SX_OP_TRIAD, wx, wy, wo, 3.0, future=False)
+    got = o.cpu().numpy()  # torch's stream: after the triad
+    assert_bitwise(got, oracle.triad(hx.numpy(), hy.numpy(), 3.0), "ordered with torch")
+    for w in (wx, wy, wo):
+        sx.sx_free(w)
+    sx.sx_executor_destroy(e)
+    sx.sx_target_destroy(t)
