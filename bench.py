@@ -507,11 +507,12 @@ def small_n_section(sx, torch, device=0, passes=100, sizes=(1 << 10, 1 << 14, 1 
 def overlap_section(sx, torch, device=0, sets=4, passes=20, sizes=(1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24)):
     """Asynchronous execution over several targets (Section 3.3 async_execute/bulk_async_execute,
     Section 4.2: a target is a device and a stream).  `sets` independent FP64 STREAM array sets,
-    `passes` passes each, enqueued pass by pass with PAR_TASK executors and waited for at the end:
-    either every set on one target (one stream: the sets run one after another) or each set on a
-    target of its own (one stream each, free to overlap).  Same memory in both modes (the one-
-    stream mode borrows the sets' arrays).  Host clock from the first enqueue to the last wait;
-    results checked against the oracle (all elements up to 2^20, the first 4096 above)."""
+    `passes` passes each (one sx_stream_iter call per set, replayed from CUDA graphs), enqueued with
+    PAR_TASK executors and waited for at the end: either every set on one target (one stream: the
+    sets run one after another) or each set on a target of its own (one stream each, free to
+    overlap).  Same memory in both modes (the one-stream mode borrows the sets' arrays).  Host clock
+    from the first enqueue to the last wait (graphs captured by untimed warm-up runs); results
+    checked against the oracle (all elements up to 2^20, the first 4096 above)."""
     import oracle
     import stream_inputs as si
     tgts = [sx.sx_target_create(device) for _ in range(sets)]
@@ -532,12 +533,11 @@ def overlap_section(sx, torch, device=0, sets=4, passes=20, sizes=(1 << 16, 1 <<
         def run(concurrent):
             seed()
             t0 = time.perf_counter()
-            for _ in range(passes):
-                for k in range(sets):
-                    if concurrent:
-                        sx.sx_stream_iter(execs[k], *owned[k], Q, 1)
-                    else:
-                        sx.sx_stream_iter(execs[0], *borrowed[k], Q, 1)
+            for k in range(sets):
+                if concurrent:
+                    sx.sx_stream_iter(execs[k], *owned[k], Q, passes)
+                else:
+                    sx.sx_stream_iter(execs[0], *borrowed[k], Q, passes)
             for ex in execs:
                 sx.sx_executor_wait(ex)
             return time.perf_counter() - t0
@@ -571,8 +571,8 @@ def overlap_section(sx, torch, device=0, sets=4, passes=20, sizes=(1 << 16, 1 <<
         sx.sx_executor_destroy(ex)
     for tt in tgts:
         sx.sx_target_destroy(tt)
-    return {"what": f"{sets} independent FP64 STREAM sets x {passes} passes, PAR_TASK, enqueued pass by pass; "
-                    "one target (one stream) vs one target per set; host clock incl. enqueue",
+    return {"what": f"{sets} independent FP64 STREAM sets x {passes} passes (one call per set, CUDA graphs), "
+                    "PAR_TASK; one target (one stream) vs one target per set; host clock incl. enqueue",
             "runs": rows}
 
 
