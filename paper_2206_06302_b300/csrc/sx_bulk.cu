@@ -162,7 +162,10 @@ k_stream_bulk(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_
         const uint32_t ctid = threadIdx.x - 32, ncons = blockDim.x - 32;
         for (uint64_t j = 0; j < nlocal; ++j) {
             const int s = (int)(j % (uint64_t)stages);
-            if (!mbar_wait_or_abort(&full[s], (uint32_t)((j / (uint64_t)stages) & 1), abort_v)) {
+            // one decision per warp (every lane's wait returns within the limit), so that no lane
+            // leaves the loop while the others go on to the warp barrier below
+            const bool ok = mbar_wait_or_abort(&full[s], (uint32_t)((j / (uint64_t)stages) & 1), abort_v);
+            if (!__all_sync(0xffffffffu, ok)) {
                 *abort_v = 1;
                 break;
             }
