@@ -166,3 +166,49 @@ def test_bad_items_are_rejected(target):
         sx.sx_batch_create(target, [it])
     with pytest.raises(sx.SxError):
         sx.sx_batch_create(target, [], dict(chunk_bytes=100, threads=256, blocks_per_sm=1, vec_bytes=32))
+
+
+@pytest.mark.parametrize("vec", [16, 32])
+def test_batch_products_on_every_bit_pattern(target, vec):
+    """FP64 SCALE and TRIAD items on random bit patterns (zeros, subnormals, values near the
+    overflow threshold, infinities, NaNs) with scalars that take each product variant (short and
+    long significands, subnormal, zero, infinite): every output equals the oracle wherever the
+    oracle's result is not a NaN, and is a NaN exactly where it is (a generated NaN's sign and
+    payload are unspecified).  Items start at different offsets of the vector alignment."""
+    import torch
+    n = 20011
+    x = si.words(71, n).view(np.float64).copy()
+    y = si.words(72, n).view(np.float64).copy()
+    qs = [3.0, -0.1, 1.0, 2.0 ** -1022, 5e-324, 1.7976931348623157e308, 1e300, -7.5, float("inf"), 0.0]
+    narr = 2 + 2 * len(qs)
+    buf = torch.zeros(narr * (n * 8 + 512), dtype=torch.uint8, device="cuda")  # 512: alignment + offset
+    base = buf.data_ptr()
+    at = [0]
+
+    def put(arr, off):
+        at[0] = (at[0] + 255) // 256 * 256 + 8 * off
+        p = at[0]
+        buf[p:p + arr.nbytes] = torch.from_numpy(arr.view(np.uint8)).cuda()
+        at[0] += arr.nbytes
+        return p
+
+    px, py = put(x, 1), put(y, 1)
+    items, outs = [], []
+    for k, q in enumerate(qs):
+        for op in (sx.SX_OP_SCALE, sx.SX_OP_TRIAD):
+            po = put(np.zeros(n), 1 if k % 2 else 3)
+            items.append(sx.sx_batch_item(op=op, dtype=sx.SX_F64, n=n, x=base + px, y=base + py,
+                                          out=base + po, q=q))
+            outs.append((po, op, q))
+    torch.cuda.synchronize()
+    b = sx.sx_batch_create(target, items, dict(chunk_bytes=16384, threads=256, blocks_per_sm=2, vec_bytes=vec))
+    sx.sx_batch_launch(b)
+    sx.sx_target_synchronize(target)
+    sx.sx_batch_destroy(b)
+    h = buf.cpu().numpy()
+    for po, op, q in outs:
+        got = h[po:po + 8 * n].view(np.float64)
+        want = oracle.apply(OPN[op], x, y, q)
+        ok = ~np.isnan(want)
+        assert_bitwise(got[ok], want[ok], f"{OPN[op]} q={q}")
+        assert np.array_equal(np.isnan(got), np.isnan(want)), f"{OPN[op]} q={q} NaN positions"
