@@ -228,3 +228,29 @@ def test_release_during_a_read_waits_for_the_read(target):
         sx.sx_server_release(s, rb)
     finally:
         sx.sx_server_destroy(s)
+
+
+@pytest.mark.parametrize("mode", [sx.SX_SERVE_CONTINUOUS, sx.SX_SERVE_FIFO])
+def test_requests_with_special_scalars(target, mode):
+    """FP64 and FP32 scale/triad requests whose scalar is infinite, zero, subnormal, huge or has
+    a long significand: results equal the oracle (NaN positions as NaN) in both modes."""
+    qs = [float("inf"), -0.0, 5e-324, 2.0 ** -1022, 1.7976931348623157e308, 1.0 / 3.0, -7.5]
+    reqs = []
+    for k, q in enumerate(qs):
+        for op in (sx.SX_OP_SCALE, sx.SX_OP_TRIAD):
+            for dt in (sx.SX_F64, sx.SX_F32):
+                reqs.append(dict(op=op, dtype=dt, n=1000 + 37 * k, q=q, seed_x=500 + k, seed_y=600 + k,
+                                 lo=-1.0, hi=1.0))
+    s = sx.sx_server_create(target, budget_bytes=1 << 28, mode=mode)
+    try:
+        ids = [sx.sx_server_submit(s, **r) for r in reqs]
+        for rid, r in zip(ids, reqs):
+            assert sx.sx_server_wait(s, rid, 60000)["state"] == sx.SX_REQ_DONE
+            got = _read(s, rid, 2, r)
+            want = _expected(r)[2]
+            ok = ~np.isnan(want)
+            assert np.array_equal(got[ok].view(np.uint8), want[ok].view(np.uint8)), (r["q"], OPN[r["op"]])
+            assert np.array_equal(np.isnan(got), np.isnan(want)), (r["q"], OPN[r["op"]])
+            sx.sx_server_release(s, rid)
+    finally:
+        sx.sx_server_destroy(s)
