@@ -205,9 +205,18 @@ __device__ __forceinline__ uint64_t splitmix_word(uint64_t seed, uint64_t i) {
 
 // lo + span*u with u = (w >> 11) 2^-53 (binary64) or (w >> 40) 2^-24 (binary32), each step
 // rounded to nearest even; span = RN(hi - lo) is computed by the caller in the same type.
+// The binary64 u is built exactly from the word's bits: with m the low 52 bits of w >> 11,
+// D = 0.5 + m 2^-53 lies in [0.5, 1), and u = D when the top bit of w is set, else D - 0.5
+// (exact by Sterbenz); one FP64 subtraction instead of a 64-bit conversion and a product.
+__device__ __forceinline__ double seeded_u53(uint64_t w) {
+    const uint32_t wl = (uint32_t)w, wh = (uint32_t)(w >> 32);
+    const uint32_t dlo = __funnelshift_r(wl, wh, 11);
+    const uint32_t dhi = ((wh >> 11) & 0xFFFFFu) | 0x3FE00000u;
+    const uint32_t chi = (wh >> 31) ? 0u : 0x3FE00000u;  // 0.0 or 0.5
+    return __dsub_rn(__hiloint2double((int)dhi, (int)dlo), __hiloint2double((int)chi, 0));
+}
 __device__ __forceinline__ double seeded_value(uint64_t w, double lo, double span) {
-    const double u = __dmul_rn(__ull2double_rn(w >> 11), 0x1p-53);
-    return __dadd_rn(lo, __dmul_rn(span, u));
+    return __dadd_rn(lo, __dmul_rn(span, seeded_u53(w)));
 }
 __device__ __forceinline__ float seeded_value(uint64_t w, float lo, float span) {
     const float u = __fmul_rn(__uint2float_rn((uint32_t)(w >> 40)), 0x1p-24f);
