@@ -589,6 +589,24 @@ int sx_batch_launch(sx_batch *b) {
     return SX_OK;
 }
 
+int sx_batch_launch_async(sx_batch *b, sx_future **fut) {
+    if (!b || !fut) return fail(SX_ERR_INVALID, "NULL argument");
+    *fut = nullptr;
+    DeviceScope ds(b->t->device);
+    sx_future *f = nullptr;
+    SX_TRY(new_future(b->t, &f));
+    cudaError_t e = cudaEventRecord(f->start, b->t->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->t->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(f->end, b->t->stream);
+    if (e != cudaSuccess) {
+        sx_future_destroy(f);
+        return cuda_fail(e, "batch launch");
+    }
+    b->last_was_percall = false;
+    *fut = f;
+    return SX_OK;
+}
+
 int sx_batch_launch_percall(sx_batch *b, const sx_launch_cfg *cfg) {
     if (!b) return fail(SX_ERR_INVALID, "batch is NULL");
     DeviceScope ds(b->t->device);

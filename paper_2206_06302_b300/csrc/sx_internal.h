@@ -179,6 +179,8 @@ int validate_cfg(const sx_target *t, int op, const sx_launch_cfg &cfg);
 int launch_selftest(const sx_target *t, cudaStream_t stream, int64_t limit_us);
 // Reads and clears the target's device error word.
 int check_device_error(const sx_target *t);
+// A future on target `t` with its two events created, not yet recorded (sx_runtime.cpp).
+int new_future(sx_target *t, sx_future **out);
 
 // ---- batched kernel over item lists built per launch (sx_batch.cu) ----------------------------
 // Staging of one launch: pinned host tables, device tables, and an event recorded after the

@@ -102,6 +102,8 @@ int finish_call(sx_executor *e) {
     return SX_OK;
 }
 
+}  // namespace
+
 int new_future(sx_target *t, sx_future **out) {
     sx_future *f = new (std::nothrow) sx_future();
     if (!f) return fail(SX_ERR_OOM, "host allocation failed");
@@ -117,7 +119,6 @@ int new_future(sx_target *t, sx_future **out) {
     return SX_OK;
 }
 
-}  // namespace
 }  // namespace sx
 
 using namespace sx;

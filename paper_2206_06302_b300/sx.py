@@ -149,6 +149,7 @@ _PROTOS = {
     "sx_transform_u8": [P, I, P, P],
     "sx_batch_create": [P, C.POINTER(sx_batch_item), SZ, C.POINTER(sx_batch_cfg), PP],
     "sx_batch_launch": [P],
+    "sx_batch_launch_async": [P, PP],
     "sx_batch_launch_percall": [P, C.POINTER(sx_launch_cfg)],
     "sx_batch_set_record": [P, I],
     "sx_batch_completion_ns": [P, C.POINTER(C.c_uint64), SZ],
@@ -415,6 +416,13 @@ def sx_batch_create(t, items, cfg=None):
 
 def sx_batch_launch(b) -> None:
     _check(lib.sx_batch_launch(b), "sx_batch_launch")
+
+
+def sx_batch_launch_async(b) -> int:
+    """bulk_async_execute: launch the batch and return a future (destroy it when done)."""
+    f = C.c_void_p()
+    _check(lib.sx_batch_launch_async(b, C.byref(f)), "sx_batch_launch_async")
+    return f.value
 
 
 def sx_batch_launch_percall(b, cfg=None) -> None:

@@ -212,3 +212,24 @@ def test_batch_products_on_every_bit_pattern(target, vec):
         ok = ~np.isnan(want)
         assert_bitwise(got[ok], want[ok], f"{OPN[op]} q={q}")
         assert np.array_equal(np.isnan(got), np.isnan(want)), f"{OPN[op]} q={q} NaN positions"
+
+
+def test_bulk_async_execute_future(target):
+    """sx_batch_launch_async (Listing 2's bulk_async_execute): the future completes once every
+    item has run, reports the launch's device time, and the outputs equal the oracle's."""
+    import torch
+    w = Workload(200, seed=14)
+    b = sx.sx_batch_create(target, w.items())
+    for rep in range(2):
+        w.clear_outputs()
+        torch.cuda.synchronize()
+        f = sx.sx_batch_launch_async(b)
+        sx.sx_future_wait(f, 60000)
+        assert sx.sx_future_test(f)
+        assert 0.0 < sx.sx_future_elapsed_ms(f) < 10000.0
+        sx.sx_future_destroy(f)
+        w.check(f"async launch {rep}")
+    sx.sx_batch_destroy(b)
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_batch_launch_async(None)
+    assert ei.value.status == sx.SX_ERR_INVALID
