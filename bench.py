@@ -198,14 +198,28 @@ def run_reference(args):
 # GPU legs
 # ----------------------------------------------------------------------------------------------
 
-def stream_kernels(sx, torch, t, stream, e, dtype_code, n, steps, warmup, seed_instance):
-    """Per-kernel device times of `steps` STREAM passes; returns dict and total elapsed ms."""
+def stream_kernels(sx, torch, t, stream, e, dtype_code, n, steps, warmup, seed_instance, q=Q,
+                   base_seed=None, init="uniform", doubling=False):
+    """Arrays, pass sequence and per-pass events of `steps` timed STREAM passes.  init "uniform":
+    seeded values in [-1, 1); "closed-form": a = 1, b = 2, c = 0.  doubling: a is doubled once
+    after construction, as classic STREAM does before its timed loop."""
     import stream_inputs as si
+    base_seed = si.BASE_SEED if base_seed is None else base_seed
     es = 8 if dtype_code == sx.SX_F64 else 4
     arrs = [sx.sx_alloc(t, dtype_code, n) for _ in range(3)]
-    for k, arr in enumerate(arrs):
-        sx.sx_seed_uniform(arr, si.array_seed(si.BASE_SEED, k, seed_instance), -1.0, 1.0)
     a, b, c = arrs
+
+    def construct():
+        if init == "closed-form":
+            for arr, v in zip(arrs, (1.0, 2.0, 0.0)):
+                sx.sx_bulk_construct(arr, v)
+        else:
+            for k, arr in enumerate(arrs):
+                sx.sx_seed_uniform(arr, si.array_seed(base_seed, k, seed_instance), -1.0, 1.0)
+        if doubling:
+            sx.sx_execute_async(e[sx.SX_OP_SCALE], sx.SX_OP_SCALE, a, None, a, 2.0, future=False)
+
+    construct()
     seq = [("copy", sx.SX_OP_COPY, a, None, c), ("scale", sx.SX_OP_SCALE, c, None, b),
            ("add", sx.SX_OP_ADD, a, b, c), ("triad", sx.SX_OP_TRIAD, b, c, a)]
     count = [0]
@@ -215,21 +229,19 @@ def stream_kernels(sx, torch, t, stream, e, dtype_code, n, steps, warmup, seed_i
         # inf near k = 262).  Every 100 passes the arrays are constructed again, between the
         # per-pass events, so it is not in the timed sum.
         if count[0] and count[0] % RESEED_EVERY == 0:
-            for k, arr in enumerate(arrs):
-                sx.sx_seed_uniform(arr, si.array_seed(si.BASE_SEED, k, seed_instance), -1.0, 1.0)
+            construct()
         count[0] += 1
         if evs is not None:
             evs[0].record(stream)
         for k, (_, op, x, y, o) in enumerate(seq):
-            sx.sx_execute_async(e[op], op, x, y, o, Q, future=False)
+            sx.sx_execute_async(e[op], op, x, y, o, q, future=False)
             if evs is not None:
                 evs[k + 1].record(stream)
 
     for _ in range(warmup):
         one_pass()
     count[0] = 0
-    for k, arr in enumerate(arrs):
-        sx.sx_seed_uniform(arr, si.array_seed(si.BASE_SEED, k, seed_instance), -1.0, 1.0)
+    construct()
     torch.cuda.synchronize()
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
     return arrs, seq, one_pass, events, es
@@ -754,20 +766,24 @@ def run_ours(args):
                     sx.sx_tune(t, op, dcode, tune_n)
         if args.tune_cache:
             sx.sx_tune_save(args.tune_cache)
-    e_auto = sx.sx_executor_create(t, sx.SX_PAR_TASK)
+    forced = {"vector": dict(variant=sx.SX_VARIANT_VECTOR), "bulk": dict(variant=sx.SX_VARIANT_BULK)}
+    e_auto = sx.sx_executor_create(t, sx.SX_PAR_TASK, forced.get(args.variant))
     execs = {}  # per dtype and op: an executor fixed to the shape resolved at tune_n
     for dcode, dname in ((sx.SX_F64, "f64"), (sx.SX_F32, "f32")):
         tuned[dname] = {name: sx.sx_executor_resolve(e_auto, op, dcode, tune_n) for name, op in names}
         execs[dcode] = {op: sx.sx_executor_create(t, sx.SX_PAR_TASK, tuned[dname][name])
                         for name, op in names}
     e = e_auto
+    main_code, main_name = (sx.SX_F32, "f32") if args.dtype == "f32" else (sx.SX_F64, "f64")
+    q = args.q
 
     peak, peak_kind = _measured_peaks()
     out = {}
 
-    # ---- the timed region: FP64 STREAM passes ------------------------------------------------
+    # ---- the timed region: STREAM passes (FP64 unless --dtype f32) ---------------------------
     arrs, seq, one_pass, events, es = stream_kernels(
-        sx, torch, t, stream, execs[sx.SX_F64], sx.SX_F64, n, args.steps, args.warmup, rank)
+        sx, torch, t, stream, execs[main_code], main_code, n, args.steps, args.warmup, rank, q,
+        args.seed, args.init, args.stream_doubling)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -805,12 +821,13 @@ def run_ours(args):
 
     # ---- FP32 per-kernel figures (same shape, fewer steps) -----------------------------------
     kernels_f32 = None
-    if not args.quick:
+    if not args.quick and main_code == sx.SX_F64:
         for arr in arrs:
             sx.sx_free(arr)
         steps32 = max(3, min(args.steps, 200))
         arrs, seq, one_pass, ev32, es32 = stream_kernels(
-            sx, torch, t, stream, execs[sx.SX_F32], sx.SX_F32, n, steps32, args.warmup, rank)
+            sx, torch, t, stream, execs[sx.SX_F32], sx.SX_F32, n, steps32, args.warmup, rank, q,
+            args.seed, args.init, args.stream_doubling)
         for s in range(steps32):
             one_pass(ev32[s])
         torch.cuda.synchronize()
@@ -828,23 +845,24 @@ def run_ours(args):
     if not args.quick and args.e2e_steps > 0:
         import stream_inputs as si
         host = []
+        tdt, ndt = (torch.float32, np.float32) if main_code == sx.SX_F32 else (torch.float64, np.float64)
         for k in range(3):
-            h = torch.empty(n, dtype=torch.float64, pin_memory=True)
-            h.numpy()[:] = si.uniform(si.array_seed(si.BASE_SEED, k, rank), n, np.float64) if k == 0 \
-                else 0.0
+            h = torch.empty(n, dtype=tdt, pin_memory=True)
+            h.numpy()[:] = si.uniform(si.array_seed(si.BASE_SEED if args.seed is None else args.seed, k, rank),
+                                      n, ndt) if k == 0 else 0.0
             host.append(h)
-        dev = [sx.sx_alloc(t, sx.SX_F64, n) for _ in range(3)]
-        esync = sx.sx_executor_create(t, sx.SX_PAR)
-        sx.sx_stream_host(esync, *(h.data_ptr() for h in host), *dev, Q, 1)  # warm
+        dev = [sx.sx_alloc(t, main_code, n) for _ in range(3)]
+        esync = sx.sx_executor_create(t, sx.SX_PAR, forced.get(args.variant))
+        sx.sx_stream_host(esync, *(h.data_ptr() for h in host), *dev, q, 1)  # warm
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            sx.sx_stream_host(esync, *(h.data_ptr() for h in host), *dev, Q, 1)
+            sx.sx_stream_host(esync, *(h.data_ptr() for h in host), *dev, q, 1)
         el = time.perf_counter() - t0
         e2e_gbs, el_ms = job_throughput(dist, el * 1e3, step_bytes, args.e2e_steps, world, "cuda")
         e2e = {"value": round(e2e_gbs, 2), "unit": "GB/s",
-               "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 3 * n * 8,
+               "h2d_bytes_per_step": 3 * n * es, "d2h_bytes_per_step": 3 * n * es,
                "steps": args.e2e_steps,
                "what": "sx_stream_host: h2d a,b,c + one pass + d2h a,b,c from pinned host memory, "
                        "pipelined in 32 MiB chunks over 3 streams; host clock"}
@@ -886,11 +904,13 @@ def run_ours(args):
     triad_ms = per["triad"] / args.steps
     achieved = 3 * n * es / (triad_ms * 1e-3) / 1e9
     traffic = None
-    same_kernel = all(tuned["f64"]["triad"].get(k) == v for k, v in NCU_TRAFFIC["cfg"].items())
+    # the captured traffic holds for the captured case only: FP64, q = 3, this n and launch shape
+    same_kernel = main_code == sx.SX_F64 and q == Q and \
+        all(tuned["f64"]["triad"].get(k) == v for k, v in NCU_TRAFFIC["cfg"].items())
     if NCU_TRAFFIC["bytes"] and NCU_TRAFFIC["source_sha256"] == _kernel_source_sha() \
             and NCU_TRAFFIC["n"] == n and same_kernel:
         traffic = NCU_TRAFFIC["bytes"]
-    roofline = {"bound": "hbm", "kernel": "triad f64", "achieved": round(achieved, 1),
+    roofline = {"bound": "hbm", "kernel": f"triad {main_name}", "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "frac_nominal_8TBs": round(achieved / NOMINAL_HBM_GBS, 4),
                 "algorithmic_bytes_per_launch": 3 * n * es, "traffic": traffic}
@@ -899,15 +919,22 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic: seeded SplitMix64 uniform [-1,1), constructed on the device",
-            "config": {"workload": "STREAM FP64 n=2^27 per array (1 GiB each), q=3; step = one pass "
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": main_name,
+            "data": ("synthetic: a=1, b=2, c=0" if args.init == "closed-form" else
+                     "synthetic: seeded SplitMix64 uniform [-1,1)") + ", constructed on the device" +
+                    (", a doubled once" if args.stream_doubling else ""),
+            "config": {"workload": f"STREAM {main_name.upper()} n=2^{n.bit_length() - 1} per array "
+                                   f"({n * es / 2 ** 30:g} GiB each), q={q:g}; step = one pass "
                                    "copy,scale,add,triad (4 launches)",
                        "n": n, "device": info["name"], "sm_count": info["sm_count"],
-                       "l2": "inputs larger than L2 (3 x 1 GiB vs 126 MB): no flush",
+                       "l2": ("inputs larger than L2: no flush" if 3 * n * es > info["l2_bytes"] else
+                              "inputs fit in L2 (L2-resident regime)"),
+                       "variant": args.variant, "init": args.init, "stream_doubling": args.stream_doubling,
                        "launch": tuned, "autotuned": bool(args.tune)},
             "kernels": kernels, "kernels_f32": kernels_f32, "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * args.steps + 3 * ((args.steps - 1) // RESEED_EVERY), "clocks": clk,
+            "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 4 * args.steps + (3 + int(args.stream_doubling)) * ((args.steps - 1) // RESEED_EVERY),
+            "clocks": clk,
         }
         line.update(extra)
         print(json.dumps(line), flush=True)
@@ -927,7 +954,18 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=1 << 27)
+    ap.add_argument("--n", type=int, default=1 << 27,
+                    help="elements per array; the per-pass events include host launch time once a "
+                         "kernel runs shorter than its launch (below ~2^22): use --sweep there")
+    ap.add_argument("--dtype", choices=["f64", "f32"], default="f64", help="type of the timed STREAM passes")
+    ap.add_argument("--q", type=float, default=Q, help="STREAM's scalar (Listing 4: 3.0)")
+    ap.add_argument("--seed", type=int, default=None, help="base seed of the seeded inputs")
+    ap.add_argument("--init", choices=["uniform", "closed-form"], default="uniform",
+                    help="seeded uniform [-1,1) inputs, or a=1, b=2, c=0")
+    ap.add_argument("--stream-doubling", action="store_true",
+                    help="double a once after construction, as classic STREAM does before timing")
+    ap.add_argument("--variant", choices=["auto", "vector", "bulk"], default="auto",
+                    help="kernel family of the timed passes (auto: the tuner table)")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the step benchmark: the size sweep, vector vs TMA bulk staging")
     ap.add_argument("--sweep-lo", type=int, default=10)

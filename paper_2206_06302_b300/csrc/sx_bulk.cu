@@ -21,6 +21,10 @@
 // Alignment: every bulk copy starts on a 16-byte boundary and moves a multiple of 16 bytes.
 // Elements before the first 16-byte boundary and after the last whole 16 bytes are done one
 // by one.  Arrays whose addresses differ modulo 16 bytes take the VECTOR family instead.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "sx_device.cuh"
 #include "sx_internal.h"
 
@@ -221,6 +225,33 @@ k_stream_bulk(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_
     }
 }
 
+// Per device and kernel instantiation: the dynamic shared memory limit already raised, and the
+// resident blocks per SM of each (threads, shared memory) shape.  Setting the attribute and
+// querying occupancy cost several microseconds of host time, more than a small launch runs.
+struct BulkKernelState {
+    size_t smem_limit = 0;
+    std::map<std::pair<int, size_t>, int> occupancy;
+};
+std::mutex g_bulk_mu;
+std::map<std::pair<int, const void *>, BulkKernelState> g_bulk_state;
+
+int bulk_prepare(int device, const void *kern, int threads, size_t smem, int *occ) {
+    std::lock_guard<std::mutex> g(g_bulk_mu);
+    BulkKernelState &st = g_bulk_state[{device, kern}];
+    if (smem > st.smem_limit) {
+        SX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        st.smem_limit = smem;
+    }
+    auto it = st.occupancy.find({threads, smem});
+    if (it == st.occupancy.end()) {
+        int o = 0;
+        SX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, threads, smem));
+        it = st.occupancy.emplace(std::make_pair(threads, smem), o).first;
+    }
+    *occ = it->second;
+    return SX_OK;
+}
+
 template <int OP, class T>
 int launch_bulk_t(const sx_target *t, cudaStream_t st, const T *x, const T *y, T *out, size_t n, T q,
                   const sx_launch_cfg &c) {
@@ -255,11 +286,8 @@ int launch_bulk_t(const sx_target *t, cudaStream_t st, const T *x, const T *y, T
             default: break;
         }
     }
-    // raise this instantiation's dynamic shared memory limit (cheap; repeated per launch so
-    // that every device the kernel runs on has it)
-    SX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    SX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, c.threads, smem));
+    SX_TRY(bulk_prepare(t->device, (const void *)kern, c.threads, smem, &occ));
     if (occ < 1) return fail(SX_ERR_INVALID, "BULK shape does not fit on an SM (%zu B shared)", smem);
     const int bps = c.blocks_per_sm < occ ? c.blocks_per_sm : occ;
     const uint64_t ntiles = (nbody + tile_elems - 1) / tile_elems;
