@@ -582,6 +582,7 @@ int sx_batch_create(sx_target *t, const sx_batch_item *items, size_t count, cons
 }
 
 int sx_batch_launch(sx_batch *b) {
+    TraceRange tr("sx_batch_launch");
     if (!b) return fail(SX_ERR_INVALID, "batch is NULL");
     DeviceScope ds(b->t->device);
     SX_CUDA(cudaGraphLaunch(b->exec, b->t->stream));
@@ -590,6 +591,7 @@ int sx_batch_launch(sx_batch *b) {
 }
 
 int sx_batch_launch_async(sx_batch *b, sx_future **fut) {
+    TraceRange tr("sx_batch_launch_async");
     if (!b || !fut) return fail(SX_ERR_INVALID, "NULL argument");
     *fut = nullptr;
     DeviceScope ds(b->t->device);
@@ -608,6 +610,7 @@ int sx_batch_launch_async(sx_batch *b, sx_future **fut) {
 }
 
 int sx_batch_launch_percall(sx_batch *b, const sx_launch_cfg *cfg) {
+    TraceRange tr("sx_batch_launch_percall");
     if (!b) return fail(SX_ERR_INVALID, "batch is NULL");
     DeviceScope ds(b->t->device);
     cudaStream_t s = b->t->stream;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cstdint>
@@ -30,6 +31,15 @@ int cuda_fail(cudaError_t e, const char *what);
         int s_ = (call);                  \
         if (s_ != SX_OK) return s_;       \
     } while (0)
+
+// An NVTX range named after the API call for its scope (header-only NVTX3: a no-op unless a
+// tool such as ncu --nvtx is attached).  Profiles can then be filtered by call.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Makes the target's device current for the scope of one API call.
 struct DeviceScope {

@@ -505,6 +505,7 @@ int sx_future_destroy(sx_future *f) {
 
 // ---- algorithms ----------------------------------------------------------------------------
 int sx_execute(sx_executor *e, sx_op op, const sx_array *x, const sx_array *y, sx_array *out, double q) {
+    TraceRange tr("sx_execute");
     SX_TRY(check_operands(e, op, x, y, out));
     DeviceScope ds(e->t->device);
     SX_TRY(enqueue_op(e, op, x, y, out, q));
@@ -513,6 +514,7 @@ int sx_execute(sx_executor *e, sx_op op, const sx_array *x, const sx_array *y, s
 
 int sx_execute_async(sx_executor *e, sx_op op, const sx_array *x, const sx_array *y, sx_array *out,
                      double q, sx_future **fut) {
+    TraceRange tr("sx_execute_async");
     if (fut) *fut = nullptr;
     SX_TRY(check_operands(e, op, x, y, out));
     DeviceScope ds(e->t->device);
@@ -629,6 +631,7 @@ static cudaGraphExec_t pass_graph(sx_executor *e, sx_array *a, sx_array *b, sx_a
 constexpr int kGraphPasses = 16;
 
 int sx_stream_iter(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double q, int iters) {
+    TraceRange tr("sx_stream_iter");
     SX_TRY(check_stream_arrays(e, a, b, c, iters));
     DeviceScope ds(e->t->device);
     sx_launch_cfg cfg[4];
@@ -663,6 +666,7 @@ int sx_stream_iter(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double
 }
 
 int sx_stream_fused(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double q, int iters) {
+    TraceRange tr("sx_stream_fused");
     SX_TRY(check_stream_arrays(e, a, b, c, iters));
     DeviceScope ds(e->t->device);
     // the chain is four binary64 operations per pass, two of them products: by default the
@@ -679,6 +683,7 @@ int sx_stream_fused(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, doubl
 // copy, `iters` whole-array passes and one copy back.
 int sx_stream_host(sx_executor *e, void *ha, void *hb, void *hc, sx_array *a, sx_array *b, sx_array *c,
                    double q, int iters) {
+    TraceRange tr("sx_stream_host");
     SX_TRY(check_stream_arrays(e, a, b, c, iters));
     if (!ha || !hb || !hc) return fail(SX_ERR_INVALID, "host pointer is NULL");
     sx_target *t = e->t;

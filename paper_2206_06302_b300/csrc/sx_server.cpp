@@ -321,6 +321,7 @@ int enqueue_fifo(sx_server *s, Request *q, Step &st) {
 //                first, shortest first, and get all of it; the rest of the budget goes to the
 //                others in admission order.
 int launch_step(sx_server *s, bool *launched) {
+    TraceRange tr("sx_server step");
     *launched = false;
     struct Want {
         Request *q;

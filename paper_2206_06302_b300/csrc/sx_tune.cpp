@@ -242,6 +242,7 @@ using namespace sx;
 extern "C" {
 
 int sx_tune(sx_target *t, sx_op op, sx_dtype dtype, size_t n, sx_launch_cfg *best_out, float *gbs) {
+    TraceRange tr("sx_tune");
     if (!t) return fail(SX_ERR_INVALID, "target is NULL");
     if (op < SX_OP_COPY || op > SX_OP_TRIAD) return fail(SX_ERR_INVALID, "op %d is not COPY..TRIAD", (int)op);
     if (dtype != SX_F32 && dtype != SX_F64) return fail(SX_ERR_DTYPE, "tuner takes F32 or F64");
