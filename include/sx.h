@@ -409,7 +409,7 @@ typedef struct sx_request {
 } sx_request;
 
 enum { SX_REQ_QUEUED = 0, SX_REQ_ACTIVE = 1, SX_REQ_DONE = 2, SX_REQ_REJECTED = 3,
-       SX_REQ_RELEASED = 4 };
+       SX_REQ_RELEASED = 4, SX_REQ_CANCELLED = 5 };
 typedef struct sx_request_status {
     int32_t state;        /* SX_REQ_*                                                      */
     int32_t status;       /* SX_OK, or why it was rejected (SX_ERR_OOM: larger than arena)  */
@@ -427,6 +427,7 @@ typedef struct sx_server_stats {
     double busy_seconds;      /* host time with at least one step in flight                 */
     double host_step_seconds;  /* CONTINUOUS: host time spent building and launching steps */
     double host_admit_seconds; /* host time spent in admission passes                      */
+    uint64_t cancelled;        /* requests cancelled (sx_server_cancel)                     */
 } sx_server_stats;
 
 /* Start a server thread on the target (its stream carries every launch).  Thread-safe calls:
@@ -440,7 +441,8 @@ int sx_server_submit(sx_server *s, const sx_request *r, uint64_t *id);
 int sx_server_replay(sx_server *s, const sx_request *reqs, const double *t_arrival, size_t count,
                      uint64_t *ids);
 int sx_server_poll(sx_server *s, uint64_t id, sx_request_status *st);
-/* Wait until the request is DONE or REJECTED (SX_ERR_TIMEOUT after timeout_ms >= 0). */
+/* Wait until the request is DONE, REJECTED, RELEASED or CANCELLED (SX_ERR_TIMEOUT after
+ * timeout_ms >= 0). */
 int sx_server_wait(sx_server *s, uint64_t id, int64_t timeout_ms, sx_request_status *st);
 /* Copy n elements of a DONE request's array (0 = x, 1 = y, 2 = out) to host memory; returns
  * once the copy is complete.  Reads from several threads may run at once. */
@@ -449,6 +451,11 @@ int sx_server_read(sx_server *s, uint64_t id, int which, void *host, size_t n);
  * reads fail); if reads of it are in progress on other threads, the memory is freed when the
  * last of them ends. */
 int sx_server_release(sx_server *s, uint64_t id);
+/* Cancel a request.  QUEUED: it leaves the queue at once.  ACTIVE: no further work of it is
+ * launched, and its arena memory is freed once the steps already holding its work have
+ * completed; it is then CANCELLED (sx_server_wait returns).  Finished requests:
+ * SX_ERR_STATE (release a DONE one instead).  Releasing a CANCELLED request does nothing. */
+int sx_server_cancel(sx_server *s, uint64_t id);
 int sx_server_stats_get(sx_server *s, sx_server_stats *st);
 /* Finish all admitted work, reject what is still queued, stop the thread, free the arena. */
 int sx_server_destroy(sx_server *s);

@@ -114,6 +114,8 @@ struct Request {
     int bypassed = 0;         // admission: times a later request was admitted first
     uint64_t admit_seq = 0;   // order of admission
     uint64_t inputs_step = 0; // step that holds the last piece of the inputs construction
+    bool cancel = false;      // sx_server_cancel: no further work; CANCELLED once none is in flight
+    uint64_t last_step = 0;   // CONTINUOUS: the last step that holds a piece of this request
     int readers = 0;          // sx_server_read copies in progress from the request's arrays
     bool free_deferred = false;  // released while being read: the last reader frees the arrays
 };
@@ -155,6 +157,7 @@ struct sx_server {
     std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
     std::deque<Request *> waiting;
     std::vector<Request *> active;
+    std::vector<Request *> cancelling;  // cancelled mid-phase: freed once their last step retires
     std::deque<Step> inflight;
     std::vector<StepSlot> slots;
     // CONTINUOUS completion reports: the host-mapped word the last block of each step writes its
@@ -381,6 +384,7 @@ int launch_step(sx_server *s, bool *launched) {
     for (size_t i = 0; i < w.size(); ++i) {
         if (grant[i] == 0) continue;
         Request *q = w[i].q;
+        q->last_step = st.seq;
         const uint64_t per = phase_bytes_per_elem(*q, q->phase);
         const uint64_t elems = grant[i];
         const uint64_t lo = q->next, hi = lo + elems;
@@ -453,7 +457,18 @@ int launch_step(sx_server *s, bool *launched) {
     return SX_OK;
 }
 
-// Retire completed steps from the front of the in-flight queue.  Returns true if any retired.
+// A cancelled request with no work in flight: arrays freed, CANCELLED.
+void finalize_cancel(sx_server *s, Request *q) {
+    release_arrays(s, q);
+    q->state = SX_REQ_CANCELLED;
+    q->t_done = now_seconds();
+    s->stats.cancelled++;
+    s->admit_dirty = true;
+    s->arrivals.fetch_add(1, std::memory_order_release);
+}
+
+// Retire completed steps from the front of the in-flight queue.  Returns true if any retired
+// (or a cancelled request was finalised).
 bool retire(sx_server *s) {
     bool any = false;
     while (!s->inflight.empty()) {
@@ -475,10 +490,14 @@ bool retire(sx_server *s) {
         }
         const double now = now_seconds();
         for (Request *q : st.finishing) {
+            s->active.erase(std::find(s->active.begin(), s->active.end(), q));
+            if (q->cancel) {
+                finalize_cancel(s, q);
+                continue;
+            }
             q->state = SX_REQ_DONE;
             q->t_done = now;
             s->stats.completed++;
-            s->active.erase(std::find(s->active.begin(), s->active.end(), q));
             if (q->r.flags & SX_REQ_AUTO_RELEASE) release_arrays(s, q);
             s->admit_dirty = true;
         }
@@ -488,6 +507,16 @@ bool retire(sx_server *s) {
         else s->free_events.push_back(st.ev);
         s->inflight.pop_front();
         any = true;
+    }
+    for (size_t i = 0; i < s->cancelling.size();) {
+        Request *q = s->cancelling[i];
+        if (q->last_step <= s->retired_seq) {
+            finalize_cancel(s, q);
+            s->cancelling.erase(s->cancelling.begin() + i);
+            any = true;
+        } else {
+            ++i;
+        }
     }
     return any;
 }
@@ -531,7 +560,7 @@ void server_loop(sx_server *s) {
             s->stats.busy_seconds += now - s->busy_since;
             s->busy_since = -1;
         }
-        const bool work_pending = !s->active.empty() || !s->inflight.empty();
+        const bool work_pending = !s->active.empty() || !s->inflight.empty() || !s->cancelling.empty();
         if (s->stop && !work_pending) break;
         if (s->stop && s->error != SX_OK && s->inflight.empty()) break;
         // Between passes the lock goes to any thread that asked for it: the server thread does
@@ -827,7 +856,8 @@ int sx_server_wait(sx_server *s, uint64_t id, int64_t timeout_ms, sx_request_sta
         if (!q) {
             // a replayed request may not be registered yet
             if (id >= s->next_id) return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
-        } else if (q->state == SX_REQ_DONE || q->state == SX_REQ_REJECTED || q->state == SX_REQ_RELEASED) {
+        } else if (q->state == SX_REQ_DONE || q->state == SX_REQ_REJECTED || q->state == SX_REQ_RELEASED ||
+                   q->state == SX_REQ_CANCELLED) {
             if (st) fill_status(s, q, st);
             return SX_OK;
         }
@@ -892,6 +922,7 @@ int sx_server_release(sx_server *s, uint64_t id) {
         ApiLock g(s);
         Request *q = find(s, id);
         if (!q) return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
+        if (q->state == SX_REQ_CANCELLED) return SX_OK;  // its arrays were freed when it was cancelled
         if (q->state != SX_REQ_DONE && q->state != SX_REQ_REJECTED)
             return fail(SX_ERR_STATE, "request %llu is not finished", (unsigned long long)id);
         if (q->state == SX_REQ_DONE) q->state = SX_REQ_RELEASED;  // no new reads from here on
@@ -904,6 +935,41 @@ int sx_server_release(sx_server *s, uint64_t id) {
         s->arrivals.fetch_add(1, std::memory_order_release);
     }
     s->cv.notify_one();  // memory freed: admission may proceed
+    return SX_OK;
+}
+
+int sx_server_cancel(sx_server *s, uint64_t id) {
+    if (!s) return fail(SX_ERR_INVALID, "NULL argument");
+    {
+        ApiLock g(s);
+        Request *q = find(s, id);
+        if (!q) {
+            if (id < s->next_id) return fail(SX_ERR_STATE, "request %llu is not registered yet (replayed)",
+                                              (unsigned long long)id);
+            return fail(SX_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
+        }
+        if (q->state == SX_REQ_QUEUED) {
+            s->waiting.erase(std::find(s->waiting.begin(), s->waiting.end(), q));
+            finalize_cancel(s, q);
+        } else if (q->state == SX_REQ_ACTIVE) {
+            if (q->cancel) return SX_OK;  // already on its way out
+            q->cancel = true;
+            // pieces not all launched: no more are; the arrays are freed once the steps holding
+            // the launched ones have completed (at once if none was launched)
+            if (q->phase < 2) {
+                s->active.erase(std::find(s->active.begin(), s->active.end(), q));
+                const bool fifo = s->cfg.mode == SX_SERVE_FIFO;
+                if (fifo || q->last_step <= s->retired_seq) finalize_cancel(s, q);
+                else s->cancelling.push_back(q);
+            }
+            // otherwise it is in a step's finishing list: retire makes it CANCELLED
+        } else {
+            return fail(SX_ERR_STATE, "request %llu is finished (release it instead)", (unsigned long long)id);
+        }
+        s->arrivals.fetch_add(1, std::memory_order_release);
+    }
+    s->cv.notify_one();
+    s->done_cv.notify_all();
     return SX_OK;
 }
 

@@ -28,7 +28,7 @@ SX_VARIANT_AUTO, SX_VARIANT_VECTOR, SX_VARIANT_BULK = 0, 1, 2
 SX_FN_TO_UPPER, SX_FN_TO_LOWER = 1, 2
 SX_SERVE_CONTINUOUS, SX_SERVE_FIFO = 0, 1
 SX_SERVE_POLICY_SRPT, SX_SERVE_POLICY_FAIR, SX_SERVE_POLICY_SHORT_FIRST = 0, 1, 2
-SX_REQ_QUEUED, SX_REQ_ACTIVE, SX_REQ_DONE, SX_REQ_REJECTED, SX_REQ_RELEASED = 0, 1, 2, 3, 4
+SX_REQ_QUEUED, SX_REQ_ACTIVE, SX_REQ_DONE, SX_REQ_REJECTED, SX_REQ_RELEASED, SX_REQ_CANCELLED = 0, 1, 2, 3, 4, 5
 SX_REQ_AUTO_RELEASE = 1
 SX_NOALLOC_MAX_ITEMS, SX_NOALLOC_MAX_TILES, SX_NOALLOC_SCRATCH_BYTES = 4096, 65536, 884736
 
@@ -98,7 +98,8 @@ class sx_server_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("submitted", "admitted", "completed", "rejected",
                                           "steps", "launches", "bytes_moved", "arena_used",
                                           "arena_peak", "arena_bytes")] + [(n, C.c_double) for n in (
-                                              "busy_seconds", "host_step_seconds", "host_admit_seconds")]
+                                              "busy_seconds", "host_step_seconds", "host_admit_seconds")] + [
+        ("cancelled", C.c_uint64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -169,6 +170,7 @@ _PROTOS = {
     "sx_server_wait": [P, U64, C.c_int64, C.POINTER(sx_request_status)],
     "sx_server_read": [P, U64, I, P, SZ],
     "sx_server_release": [P, U64],
+    "sx_server_cancel": [P, U64],
     "sx_server_stats_get": [P, C.POINTER(sx_server_stats)],
     "sx_server_destroy": [P],
 }
@@ -538,6 +540,10 @@ def sx_server_read(s, rid: int, which: int, host_ptr: int, n: int) -> None:
 
 def sx_server_release(s, rid: int) -> None:
     _check(lib.sx_server_release(s, rid), "sx_server_release")
+
+
+def sx_server_cancel(s, rid: int) -> None:
+    _check(lib.sx_server_cancel(s, rid), "sx_server_cancel")
 
 
 def sx_server_stats_get(s) -> dict:

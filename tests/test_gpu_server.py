@@ -254,3 +254,40 @@ def test_requests_with_special_scalars(target, mode):
             sx.sx_server_release(s, rid)
     finally:
         sx.sx_server_destroy(s)
+
+
+@pytest.mark.parametrize("mode", [sx.SX_SERVE_CONTINUOUS, sx.SX_SERVE_FIFO])
+def test_cancel_queued_active_and_finished(target, mode):
+    """A queued request leaves the queue; an active one launches no further work and is
+    CANCELLED once the work already in flight completes, its memory freed for the next request
+    (which computes correctly in it); a finished request cannot be cancelled."""
+    n = 1 << 26
+    big = dict(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=n, q=3.0, seed_x=1, seed_y=2, lo=-1.0, hi=1.0)
+    s = sx.sx_server_create(target, budget_bytes=3 * 8 * n + (64 << 20), mode=mode)
+    try:
+        ra = sx.sx_server_submit(s, **big)
+        rb = sx.sx_server_submit(s, **dict(big, seed_x=3))  # waits: the arena holds one such request
+        assert sx.sx_server_poll(s, rb)["state"] == sx.SX_REQ_QUEUED
+        sx.sx_server_cancel(s, rb)
+        assert sx.sx_server_poll(s, rb)["state"] == sx.SX_REQ_CANCELLED
+        sx.sx_server_cancel(s, ra)  # active (or, if very fast, already cancelled at its last step)
+        assert sx.sx_server_wait(s, ra, 60000)["state"] == sx.SX_REQ_CANCELLED
+        sx.sx_server_release(s, ra)  # nothing to free: a no-op
+        with pytest.raises(sx.SxError) as ei:
+            sx.sx_server_read(s, ra, 2, np.empty(1).ctypes.data, 1)
+        assert ei.value.status == sx.SX_ERR_STATE
+        st = sx.sx_server_stats_get(s)
+        assert st["cancelled"] == 2 and st["arena_used"] == 0
+        d = dict(big, seed_x=5, seed_y=6)
+        rd = sx.sx_server_submit(s, **d)
+        assert sx.sx_server_wait(s, rd, 60000)["state"] == sx.SX_REQ_DONE
+        assert np.array_equal(_read(s, rd, 2, d).view(np.uint64), _expected(d)[2].view(np.uint64))
+        with pytest.raises(sx.SxError) as ei:
+            sx.sx_server_cancel(s, rd)
+        assert ei.value.status == sx.SX_ERR_STATE
+        sx.sx_server_release(s, rd)
+        with pytest.raises(sx.SxError) as ei:
+            sx.sx_server_cancel(s, 10 ** 9)
+        assert ei.value.status == sx.SX_ERR_INVALID
+    finally:
+        sx.sx_server_destroy(s)
