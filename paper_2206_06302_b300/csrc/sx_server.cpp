@@ -42,62 +42,12 @@
 #include <vector>
 
 #include "sx_internal.h"
+#include "sx_sched.h"
 
 namespace sx {
 namespace {
 
-constexpr size_t kAlign = 256;
-
-// First-fit allocator over [0, size) with an address-ordered, coalescing free list.
-class Arena {
-  public:
-    explicit Arena(size_t size) : size_(size) {
-        if (size) free_[0] = size;
-    }
-    bool alloc(size_t bytes, size_t *off) {
-        bytes = (bytes + kAlign - 1) / kAlign * kAlign;
-        if (bytes == 0) bytes = kAlign;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                const size_t rest = it->second - bytes;
-                const size_t at = it->first + bytes;
-                free_.erase(it);
-                if (rest) free_[at] = rest;
-                used_ += bytes;
-                peak_ = std::max(peak_, used_);
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        bytes = (bytes + kAlign - 1) / kAlign * kAlign;
-        if (bytes == 0) bytes = kAlign;
-        used_ -= bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t used() const { return used_; }
-    size_t peak() const { return peak_; }
-    size_t size() const { return size_; }
-
-  private:
-    size_t size_;
-    size_t used_ = 0, peak_ = 0;
-    std::map<size_t, size_t> free_;
-};
+using sched::Arena;
 
 struct Request {
     uint64_t id = 0;
@@ -228,7 +178,7 @@ void request_sizes(const sx_request &r, size_t bytes[3]) {
 size_t rounded_total(const size_t bytes[3]) {
     size_t t = 0;
     for (int k = 0; k < 3; ++k)
-        if (bytes[k]) t += std::max<size_t>(kAlign, (bytes[k] + kAlign - 1) / kAlign * kAlign);
+        if (bytes[k]) t += sched::arena_bytes(bytes[k]);
     return t;
 }
 
@@ -315,65 +265,21 @@ int enqueue_fifo(sx_server *s, Request *q, Step &st) {
 
 // Build and launch one CONTINUOUS step from the active requests' pending work.
 //
-// How the step's byte budget is shared (cfg.policy):
-//   SRPT         shortest remaining work first: in that order each request gets all of its
-//                current phase's remaining work until the budget is spent.
-//   FAIR         water-filling: requests with less remaining work in their phase than an equal
-//                share get all of it; the others split the rest equally.
-//   SHORT_FIRST  requests whose whole remaining work is at most a quarter of the budget go
-//                first, shortest first, and get all of it; the rest of the budget goes to the
-//                others in admission order.
+// The step's byte budget is shared by cfg.policy (sched::plan_step).
 int launch_step(sx_server *s, bool *launched) {
     TraceRange tr("sx_server step");
     *launched = false;
-    struct Want {
-        Request *q;
-        uint64_t phase_bytes;  // remaining bytes of the current phase
-        uint64_t total_bytes;  // remaining bytes of the whole request
-    };
-    std::vector<Want> w;
+    std::vector<sched::Want> w;
+    std::vector<Request *> by_key;
     for (Request *q : s->active) {
         if (q->phase >= 2) continue;
-        const uint64_t pb = (uint64_t)(q->r.n - q->next) * phase_bytes_per_elem(*q, q->phase);
         const uint64_t later = q->phase == 0 ? (uint64_t)q->r.n * phase_bytes_per_elem(*q, 1) : 0;
-        w.push_back({q, pb, pb + later});
+        w.push_back({by_key.size(), q->admit_seq, phase_bytes_per_elem(*q, q->phase), q->r.n - q->next, later});
+        by_key.push_back(q);
     }
     if (w.empty()) return SX_OK;
-    const uint64_t step_budget = (uint64_t)(uint32_t)s->cfg.chunk_bytes;
-    std::vector<uint64_t> grant(w.size(), 0);  // elements of the current phase this step
-    auto whole_units = [](uint64_t elems) { return std::max<uint64_t>(elems / 64 * 64, 64); };
-    if (s->cfg.policy == SX_SERVE_POLICY_FAIR) {
-        std::sort(w.begin(), w.end(), [](const Want &a, const Want &b) { return a.phase_bytes < b.phase_bytes; });
-        uint64_t budget = step_budget;
-        for (size_t i = 0; i < w.size(); ++i) {
-            const uint64_t per = phase_bytes_per_elem(*w[i].q, w[i].q->phase);
-            const uint64_t remaining = w[i].q->r.n - w[i].q->next;
-            grant[i] = std::min(remaining, whole_units(budget / (w.size() - i) / per));
-            budget -= std::min(budget, grant[i] * per);
-        }
-    } else {
-        if (s->cfg.policy == SX_SERVE_POLICY_SRPT) {
-            std::sort(w.begin(), w.end(), [](const Want &a, const Want &b) {
-                if (a.total_bytes != b.total_bytes) return a.total_bytes < b.total_bytes;
-                return a.q->admit_seq < b.q->admit_seq;
-            });
-        } else {
-            const uint64_t short_bytes = step_budget / 4;
-            std::sort(w.begin(), w.end(), [short_bytes](const Want &a, const Want &b) {
-                const bool sa = a.total_bytes <= short_bytes, sb = b.total_bytes <= short_bytes;
-                if (sa != sb) return sa;
-                if (sa) return a.total_bytes < b.total_bytes;
-                return a.q->admit_seq < b.q->admit_seq;
-            });
-        }
-        uint64_t budget = step_budget;
-        for (size_t i = 0; i < w.size() && budget > 0; ++i) {
-            const uint64_t per = phase_bytes_per_elem(*w[i].q, w[i].q->phase);
-            const uint64_t remaining = w[i].q->r.n - w[i].q->next;
-            grant[i] = std::min(remaining, whole_units(budget / per));
-            budget -= std::min(budget, grant[i] * per);
-        }
-    }
+    // elements of each request's current phase in this step, in the policy's order (sx_sched.h)
+    const std::vector<uint64_t> grant = sched::plan_step(s->cfg.policy, (uint64_t)(uint32_t)s->cfg.chunk_bytes, w);
     const int slot = s->free_slots.back();
     s->free_slots.pop_back();
     std::vector<sx_batch_item> items;
@@ -383,7 +289,7 @@ int launch_step(sx_server *s, bool *launched) {
     st.seq = s->step_seq + 1;
     for (size_t i = 0; i < w.size(); ++i) {
         if (grant[i] == 0) continue;
-        Request *q = w[i].q;
+        Request *q = by_key[w[i].key];
         q->last_step = st.seq;
         const uint64_t per = phase_bytes_per_elem(*q, q->phase);
         const uint64_t elems = grant[i];
