@@ -1,11 +1,12 @@
 // sx_sched.h -- the host-side scheduling of the serving loop (sx_server.cpp), free of CUDA so
-// that it is tested on the host: the arena allocator of the server's device memory and the
-// sharing of one step's byte budget between the active requests.
+// that it is tested on the host: the arena allocator of the server's device memory, admission of
+// waiting requests, and the sharing of one step's byte budget between the active requests.
 #pragma once
 
 #include <algorithm>
 #include <cstddef>
 #include <cstdint>
+#include <deque>
 #include <map>
 #include <vector>
 
@@ -97,7 +98,8 @@ inline uint64_t whole_units(uint64_t elems) { return std::max<uint64_t>(elems / 
 //                first, shortest first, and get all of it; the rest of the budget goes to the
 //                others in admission order.
 // The first request in the order always gets at least 64 elements (or all it has), so a step
-// is never empty; a grant can exceed the budget by less than 64 elements' worth.
+// is never empty; the bytes granted exceed the budget by less than 64 elements' worth per
+// request served.
 inline std::vector<uint64_t> plan_step(int policy, uint64_t budget, std::vector<Want> &w) {
     std::vector<uint64_t> grant(w.size(), 0);
     if (policy == SX_SERVE_POLICY_FAIR) {
@@ -127,6 +129,34 @@ inline std::vector<uint64_t> plan_step(int policy, uint64_t budget, std::vector<
         budget -= std::min(budget, grant[i] * w[i].per);
     }
     return grant;
+}
+
+// One admission pass over `waiting` (arrival order) into `active`, at most `slots` active and at
+// most kAdmitTries requests looked at: `fits(q)` admits q if its arrays fit (taking the memory).
+// A later request may pass one that does not fit, but a request passed kMaxBypass times blocks
+// the queue until it fits (no starvation).  Returns true if another pass should follow at once
+// (the look-ahead ran out with room left).  Q has an int `bypassed`.
+constexpr size_t kAdmitTries = 64;
+constexpr int kMaxBypass = 64;
+
+template <class Q, class Fits>
+bool admission_pass(std::deque<Q *> &waiting, std::vector<Q *> &active, size_t slots, Fits fits) {
+    std::vector<Q *> passed;  // waiting requests a later one may overtake in this pass
+    size_t tried = 0;
+    for (auto it = waiting.begin(); it != waiting.end() && tried < kAdmitTries; ++tried) {
+        if (active.size() >= slots) break;
+        Q *q = *it;
+        if (fits(q)) {
+            for (Q *p : passed) p->bypassed++;
+            active.push_back(q);
+            it = waiting.erase(it);
+            continue;
+        }
+        if (q->bypassed >= kMaxBypass) break;  // it has waited long enough: nobody passes it any more
+        passed.push_back(q);
+        ++it;
+    }
+    return !waiting.empty() && active.size() < slots && tried >= kAdmitTries;
 }
 
 }  // namespace sched

@@ -215,29 +215,14 @@ bool try_admit(sx_server *s, Request *q) {
     return true;
 }
 
-// Admission in arrival order; a later request may pass one that does not fit, but a request
-// passed 64 times blocks the queue until it fits (no starvation).
+// Admission in arrival order with bounded overtaking (sched::admission_pass).
 void admit(sx_server *s) {
     if (!s->admit_dirty) return;
     s->admit_dirty = false;
     const double t0 = now_seconds();
-    const size_t slots = (size_t)s->cfg.max_active;
-    std::vector<Request *> passed;  // waiting requests a later one may overtake in this pass
-    size_t tried = 0;
-    for (auto it = s->waiting.begin(); it != s->waiting.end() && tried < 64; ++tried) {
-        if (s->active.size() >= slots) break;
-        Request *q = *it;
-        if (try_admit(s, q)) {
-            for (Request *p : passed) p->bypassed++;
-            s->active.push_back(q);
-            it = s->waiting.erase(it);
-            continue;
-        }
-        if (q->bypassed >= 64) break;  // it has waited long enough: nobody passes it any more
-        passed.push_back(q);
-        ++it;
-    }
-    if (!s->waiting.empty() && s->active.size() < slots && tried >= 64) s->admit_dirty = true;
+    if (sched::admission_pass(s->waiting, s->active, (size_t)s->cfg.max_active,
+                              [s](Request *q) { return try_admit(s, q); }))
+        s->admit_dirty = true;
     s->stats.host_admit_seconds += now_seconds() - t0;
 }
 

@@ -154,7 +154,63 @@ static void policy_random() {
     }
 }
 
+// Admission: arrival order; later requests pass one that does not fit until it has been passed
+// kMaxBypass times, after which nothing is admitted before it; the slot limit holds; the
+// look-ahead is bounded and asks for another pass when it runs out with room left.
+struct FakeReq {
+    int id;
+    size_t bytes;
+    int bypassed = 0;
+};
+
+static void admission() {
+    using sx::sched::admission_pass;
+    std::vector<FakeReq> reqs;
+    for (int k = 0; k < 10; ++k) reqs.push_back({k, (k == 2) ? 1000u : 10u});
+    std::deque<FakeReq *> waiting;
+    for (auto &r : reqs) waiting.push_back(&r);
+    std::vector<FakeReq *> active;
+    size_t free_bytes = 100;
+    auto fits = [&](FakeReq *q) {
+        if (q->bytes > free_bytes) return false;
+        free_bytes -= q->bytes;
+        return true;
+    };
+    // request 2 does not fit: 0, 1 and 3..9 are admitted in order past it, and it is passed 7 times
+    CHECK(!admission_pass(waiting, active, 100, fits));
+    CHECK(active.size() == 9 && waiting.size() == 1 && waiting[0]->id == 2);
+    CHECK(active[0]->id == 0 && active[1]->id == 1 && active[2]->id == 3);
+    CHECK(reqs[2].bypassed == 7);
+    // once passed kMaxBypass times, nothing gets in before it
+    reqs[2].bypassed = sx::sched::kMaxBypass;
+    FakeReq late{42, 1};
+    waiting.push_back(&late);
+    CHECK(!admission_pass(waiting, active, 100, fits));
+    CHECK(waiting.size() == 2 && waiting[1]->id == 42);
+    free_bytes = 2000;  // now it fits, and the late one follows in order
+    CHECK(!admission_pass(waiting, active, 100, fits));
+    CHECK(waiting.empty() && active[active.size() - 2]->id == 2 && active.back()->id == 42);
+    // slot limit
+    std::vector<FakeReq> many(10, FakeReq{0, 1});
+    std::deque<FakeReq *> w2;
+    for (auto &r : many) w2.push_back(&r);
+    std::vector<FakeReq *> a2;
+    free_bytes = 1000;
+    CHECK(!admission_pass(w2, a2, 4, fits));
+    CHECK(a2.size() == 4 && w2.size() == 6);
+    // bounded look-ahead: 200 requests that do not fit ahead of one that does
+    std::vector<FakeReq> big(200, FakeReq{1, 1u << 30});
+    FakeReq small{2, 1};
+    std::deque<FakeReq *> w3;
+    for (auto &r : big) w3.push_back(&r);
+    w3.push_back(&small);
+    std::vector<FakeReq *> a3;
+    CHECK(admission_pass(w3, a3, 100, fits));  // ran out of look-ahead: try again
+    CHECK(a3.empty() && w3.size() == 201);
+}
+
 int main() {
+    admission();
     arena_basics();
     arena_random();
     policy_srpt();
