@@ -346,6 +346,7 @@ def batched_section(sx, torch, t, stream, args, rank):
                     f"(seeded), {nbytes / 1e9:.1f} GB moved per launch",
         "tuned": cfg, "tiles": tiles,
         "graph_ms": round(gm, 4), "graph_GB/s": round(nbytes / (gm * 1e-3) / 1e9, 1),
+        "graph_frac_measured": round(nbytes / (gm * 1e-3) / 1e9 / _measured_peaks()[0], 4),
         "percall_ms": round(pm, 4), "percall_GB/s": round(nbytes / (pm * 1e-3) / 1e9, 1),
         "speedup": round(pm / gm, 3),
         "completion_ms_p50": {"graph": round(_pct(comp_g, 50), 4), "percall": round(_pct(comp_p, 50), 4)},
@@ -415,6 +416,8 @@ def served_section(sx, torch, t, stream, args, rank):
     for mode, name in modes:
         _, stats, span = serve_run(sx, t, work, zero, budget, mode)
         out["saturation_GB/s"][name] = round(stats["bytes_moved"] / span / 1e9, 1)
+        out.setdefault("saturation_frac_measured", {})[name] = round(
+            stats["bytes_moved"] / span / 1e9 / _measured_peaks()[0], 4)
     capacity = out["saturation_GB/s"]["fifo"] * 1e9
     out["capacity_from"] = "per-call FIFO throughput at saturation"
     for load in [float(v) for v in args.serve_loads.split(",") if v]:
