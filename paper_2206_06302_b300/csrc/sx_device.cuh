@@ -186,6 +186,10 @@ __device__ __forceinline__ void xorshift_halves(uint32_t &lo, uint32_t &hi, int 
     lo ^= __funnelshift_r(lo, hi, s);
     hi ^= hi >> s;
 }
+// HIGH_ONLY: the result is exact in bits 33..63 only.  The last step z ^ (z >> 31) leaves those
+// bits as they are (the shifted term is zero there), so a caller that uses w >> 40 (binary32
+// values) skips it.
+template <bool HIGH_ONLY = false>
 __device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
     uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
     xorshift_halves(lo, hi, 30);
@@ -194,6 +198,7 @@ __device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
     hi = (uint32_t)(z >> 32);
     xorshift_halves(lo, hi, 27);
     z = (((uint64_t)hi << 32) | lo) * 0x94D049BB133111EBull;
+    if (HIGH_ONLY) return z;
     lo = (uint32_t)z;
     hi = (uint32_t)(z >> 32);
     xorshift_halves(lo, hi, 31);
@@ -297,7 +302,7 @@ __device__ __forceinline__ void seed_range(T *out, uint64_t cnt, uint64_t seed, 
         uint64_t b[E * sizeof(T) / 8];
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const uint64_t w = splitmix_mix(z);
+            const uint64_t w = splitmix_mix<sizeof(T) == 4>(z);  // binary32 uses bits 40..63 only
             z += kSplitmixGamma;
             if constexpr (sizeof(T) == 8) {
                 const double v = !PM1 ? seeded_value(w, (double)lo, (double)span)
