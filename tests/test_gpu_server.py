@@ -291,3 +291,54 @@ def test_cancel_queued_active_and_finished(target, mode):
         assert ei.value.status == sx.SX_ERR_INVALID
     finally:
         sx.sx_server_destroy(s)
+
+
+@pytest.mark.parametrize("mode", [sx.SX_SERVE_CONTINUOUS, sx.SX_SERVE_FIFO])
+def test_concurrent_clients(target, mode):
+    """Eight client threads each submit, wait for, read, check and release (or cancel) their own
+    stream of requests against one server: every completed result equals the oracle's, every
+    request ends DONE or CANCELLED, and the arena is empty at the end."""
+    import threading
+    threads, per_thread = 8, 24
+    s = sx.sx_server_create(target, budget_bytes=1 << 28, mode=mode)
+    errors, cancelled = [], [0]
+    lock = threading.Lock()
+
+    def client(k):
+        try:
+            reqs = _requests(per_thread, 900 + k, lo_exp=4, hi_exp=16)
+            rng = np.random.default_rng(k)
+            for i, r in enumerate(reqs):
+                rid = sx.sx_server_submit(s, **r)
+                if rng.random() < 0.2:
+                    try:
+                        sx.sx_server_cancel(s, rid)
+                    except sx.SxError as e:  # it may have finished already
+                        assert e.status == sx.SX_ERR_STATE
+                st = sx.sx_server_wait(s, rid, 60000)
+                if st["state"] == sx.SX_REQ_CANCELLED:
+                    with lock:
+                        cancelled[0] += 1
+                    continue
+                assert st["state"] == sx.SX_REQ_DONE, st
+                want = _expected(r)[2]
+                got = _read(s, rid, 2, r)
+                assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), (k, i)
+                sx.sx_server_release(s, rid)
+        except Exception as e:  # reported by the main thread
+            errors.append((k, repr(e)))
+
+    ts = [threading.Thread(target=client, args=(k,)) for k in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    try:
+        assert not errors, errors[:3]
+        st = sx.sx_server_stats_get(s)
+        assert st["submitted"] == threads * per_thread
+        assert st["completed"] + st["cancelled"] == threads * per_thread
+        assert st["cancelled"] == cancelled[0]
+        assert st["arena_used"] == 0
+    finally:
+        sx.sx_server_destroy(s)
