@@ -142,7 +142,9 @@ int sx_target_create(int device, sx_target **out);
  * outlive the target.  To borrow the legacy default stream (the one other libraries use when
  * they name stream 0), pass its handle cudaStreamLegacy, (void *)0x1. */
 int sx_target_create_ext(int device, void *stream, size_t budget_bytes, sx_target **out);
+/* Wait for the target's stream, then free the target (and its stream if it owns it). */
 int sx_target_destroy(sx_target *t);
+/* The target's properties and allocation accounting (hbm_free as of the call). */
 int sx_target_info_get(const sx_target *t, sx_target_info *out);
 /* The cudaStream_t the target enqueues on. */
 int sx_target_stream(const sx_target *t, void **stream);
@@ -169,6 +171,7 @@ int sx_alloc(sx_target *t, sx_dtype dtype, size_t n, sx_array **out);
 int sx_array_wrap(sx_target *t, sx_dtype dtype, void *device_ptr, size_t n, sx_array **out);
 /* Release an array and, for owned arrays, its device memory. */
 int sx_free(sx_array *a);
+/* The array's device pointer, element count and sx_dtype (any output may be NULL). */
 int sx_array_data(const sx_array *a, void **device_ptr, size_t *n, int *dtype);
 /* Owned arrays: *ok = 1 if the 256 guard bytes past the last element are untouched.  Waits
  * for the target's stream first.  Borrowed arrays: *ok = 1. */
@@ -202,6 +205,7 @@ typedef struct sx_executor sx_executor;
 /* `cfg` NULL (or variant AUTO) lets each call pick its launch shape (autotuner table first,
  * then the built-in default).  The executor keeps a copy of *cfg. */
 int sx_executor_create(sx_target *t, sx_policy policy, const sx_launch_cfg *cfg, sx_executor **out);
+/* Free the executor and the CUDA graphs it keeps (work it enqueued is not waited for). */
 int sx_executor_destroy(sx_executor *e);
 /* Block until all work enqueued on the executor's target has finished (then as
  * sx_target_synchronize). */
@@ -306,7 +310,9 @@ int sx_batch_launch_percall(sx_batch *b, const sx_launch_cfg *cfg);
  * completion time in ns of the device global timer relative to the launch's first work. */
 int sx_batch_set_record(sx_batch *b, int record);
 int sx_batch_completion_ns(sx_batch *b, uint64_t *t_ns, size_t count);
+/* The batch's launch shape, number of work tiles and STREAM bytes of one launch. */
 int sx_batch_info(const sx_batch *b, sx_batch_cfg *cfg, uint64_t *tiles, uint64_t *bytes);
+/* Wait for the target's stream, then free the batch's graph and tables. */
 int sx_batch_destroy(sx_batch *b);
 
 /* ---- a batch launch that allocates nothing ---------------------------------------------
@@ -352,6 +358,7 @@ int sx_tune_lookup(const sx_target *t, sx_op op, sx_dtype dtype, size_t n, sx_la
 /* Persist / restore the table as JSON (entries for other devices are kept as they are). */
 int sx_tune_save(const char *path);
 int sx_tune_load(const char *path);
+/* Empty the table (launches then use the built-in defaults until entries are added again). */
 int sx_tune_clear(void);
 
 /* ---- serving loop: continuous batching of STREAM requests on device-resident arrays ---- */
@@ -440,6 +447,7 @@ int sx_server_submit(sx_server *s, const sx_request *r, uint64_t *id);
  * after this call; ids[k] receives each request's id at once.  Returns immediately. */
 int sx_server_replay(sx_server *s, const sx_request *reqs, const double *t_arrival, size_t count,
                      uint64_t *ids);
+/* The request's current state and timestamps, without waiting. */
 int sx_server_poll(sx_server *s, uint64_t id, sx_request_status *st);
 /* Wait until the request is DONE, REJECTED, RELEASED or CANCELLED (SX_ERR_TIMEOUT after
  * timeout_ms >= 0). */
@@ -456,6 +464,7 @@ int sx_server_release(sx_server *s, uint64_t id);
  * completed; it is then CANCELLED (sx_server_wait returns).  Finished requests:
  * SX_ERR_STATE (release a DONE one instead).  Releasing a CANCELLED request does nothing. */
 int sx_server_cancel(sx_server *s, uint64_t id);
+/* Counters of the server since its creation (busy_seconds up to the call). */
 int sx_server_stats_get(sx_server *s, sx_server_stats *st);
 /* Finish all admitted work, reject what is still queued, stop the thread, free the arena. */
 int sx_server_destroy(sx_server *s);
