@@ -717,7 +717,7 @@ def run_sweep(args):
             for name, op, narr in ops:
                 for vname, e in execs.items():
                     nbytes = narr * n * es
-                    reps = int(min(2000, max(5, 4e-3 / max(nbytes / 6e12, 2e-6))))
+                    reps = int(min(2000, max(20, 4e-3 / max(nbytes / 6e12, 2e-6))))  # >= 20 timed launches per point
                     for _ in range(3):
                         sx.sx_execute_async(e, op, x, y, o, Q, future=False)
                     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
