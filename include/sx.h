@@ -265,6 +265,15 @@ int sx_stream_host(sx_executor *e, void *host_a, void *host_b, void *host_c, sx_
  * Built-in callables for U8 arrays: SX_FN_TO_UPPER (ASCII a-z -> A-Z), SX_FN_TO_LOWER. */
 enum { SX_FN_TO_UPPER = 1, SX_FN_TO_LOWER = 2 };
 int sx_transform_u8(sx_executor *e, int fn, const sx_array *in, sx_array *out);
+/* Element transform with any device callable, given as CUDA C++ source (Section 4.2: the CUDA
+ * executor runs any callable marked __device__).  `src` defines
+ *     __device__ sx_t sx_fn(sx_t x)
+ * where sx_t is the arrays' element type (float, double or unsigned char); out[i] = sx_fn(in[i]).
+ * The source is compiled at run time for the target's GPU (NVRTC, no fused multiply-add, no fast
+ * math) on first use and kept per (device, type, source).  `out` may be `in`.  SX_ERR_INVALID,
+ * with the compiler's log in sx_last_error(), if the source does not compile; SX_ERR_STATE if
+ * run-time compilation is not available.  Follows the executor's policy. */
+int sx_transform_src(sx_executor *e, const char *src, const sx_array *in, sx_array *out);
 
 /* ---- bulk execution over many independent instances (Listing 2's bulk_execute, one
  *      persistent launch captured in a CUDA graph) -------------------------------------- */

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsx.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["sx_runtime.cpp", "sx_kernels.cu", "sx_bulk.cu", "sx_batch.cu", "sx_tune.cpp",
-           "sx_server.cpp", "sx_selftest.cu"]
+           "sx_server.cpp", "sx_selftest.cu", "sx_jit.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-Wall", "-I" + INCLUDE, "-I" + CSRC]
@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             subprocess.run(cmd, check=True)
     if force or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-ldl"]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)

@@ -1,0 +1,170 @@
+// sx_jit.cpp -- element transform with a device callable given as CUDA C++ source.
+//
+// Section 4.2 lets the CUDA executor run any callable marked __device__ (nvcc compiles the
+// caller's code for the device).  Here the caller hands over the callable's source: it is placed
+// in a grid-stride element loop, compiled at run time for this GPU by NVRTC (loaded with dlopen
+// on first use, so the library does not depend on it otherwise; no fused multiply-add, no fast
+// math), loaded with the runtime's library API, and kept per (device, element type, source).
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <cstdio>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "sx_internal.h"
+
+namespace sx {
+namespace {
+
+// The NVRTC entry points used, resolved from libnvrtc at the first call.
+struct Nvrtc {
+    decltype(&nvrtcCreateProgram) create = nullptr;
+    decltype(&nvrtcCompileProgram) compile = nullptr;
+    decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+    decltype(&nvrtcGetProgramLog) log = nullptr;
+    decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+    decltype(&nvrtcGetCUBIN) cubin = nullptr;
+    decltype(&nvrtcDestroyProgram) destroy = nullptr;
+    decltype(&nvrtcGetErrorString) error_string = nullptr;
+    bool ok = false;
+};
+
+const Nvrtc &nvrtc() {
+    static Nvrtc n;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *h = nullptr;
+        for (const char *name : {"libnvrtc.so.13", "libnvrtc.so"})
+            if ((h = dlopen(name, RTLD_NOW | RTLD_LOCAL)) != nullptr) break;
+        if (!h) return;
+        n.create = (decltype(n.create))dlsym(h, "nvrtcCreateProgram");
+        n.compile = (decltype(n.compile))dlsym(h, "nvrtcCompileProgram");
+        n.log_size = (decltype(n.log_size))dlsym(h, "nvrtcGetProgramLogSize");
+        n.log = (decltype(n.log))dlsym(h, "nvrtcGetProgramLog");
+        n.cubin_size = (decltype(n.cubin_size))dlsym(h, "nvrtcGetCUBINSize");
+        n.cubin = (decltype(n.cubin))dlsym(h, "nvrtcGetCUBIN");
+        n.destroy = (decltype(n.destroy))dlsym(h, "nvrtcDestroyProgram");
+        n.error_string = (decltype(n.error_string))dlsym(h, "nvrtcGetErrorString");
+        n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy && n.error_string;
+    });
+    return n;
+}
+
+const char *type_name(int dtype) {
+    switch (dtype) {
+        case SX_F32: return "float";
+        case SX_F64: return "double";
+        case SX_U8: return "unsigned char";
+        default: return nullptr;
+    }
+}
+
+struct Compiled {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kernel = nullptr;
+};
+
+using Key = std::tuple<int, int, std::string>;  // device, dtype, source
+std::mutex g_jit_mu;
+std::map<Key, Compiled> g_jit;
+constexpr size_t kMaxCompiled = 64;
+
+// Compile `src` for the device of `t` and element type `dtype`, or take it from the cache.
+int get_kernel(const sx_target *t, int dtype, const char *src, cudaKernel_t *out) {
+    std::lock_guard<std::mutex> g(g_jit_mu);
+    const Key key{t->device, dtype, std::string(src)};
+    auto it = g_jit.find(key);
+    if (it != g_jit.end()) {
+        *out = it->second.kernel;
+        return SX_OK;
+    }
+    const Nvrtc &nv = nvrtc();
+    if (!nv.ok) return fail(SX_ERR_STATE, "run-time compilation unavailable: libnvrtc not found");
+    std::string code = "typedef ";
+    code += type_name(dtype);
+    code += " sx_t;\n#line 1 \"callable\"\n";
+    code += src;
+    code += "\nextern \"C\" __global__ void sx_user_map(const sx_t *in, sx_t *out, unsigned long long n) {\n"
+            "    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;\n"
+            "         i += (unsigned long long)gridDim.x * blockDim.x)\n"
+            "        out[i] = sx_fn(in[i]);\n"
+            "}\n";
+    char arch[64];
+    std::snprintf(arch, sizeof arch, "--gpu-architecture=sm_%d%d", t->cc_major, t->cc_minor);
+    const char *opts[] = {arch, "-fmad=false", "--std=c++17"};
+    nvrtcProgram prog = nullptr;
+    nvrtcResult r = nv.create(&prog, code.c_str(), "sx_user_map.cu", 0, nullptr, nullptr);
+    if (r != NVRTC_SUCCESS) return fail(SX_ERR_STATE, "nvrtcCreateProgram: %s", nv.error_string(r));
+    r = nv.compile(prog, 3, opts);
+    if (r != NVRTC_SUCCESS) {
+        size_t n = 0;
+        nv.log_size(prog, &n);
+        std::string log(n, '\0');
+        if (n) nv.log(prog, &log[0]);
+        nv.destroy(&prog);
+        if (log.size() > 2000) log.resize(2000);
+        return fail(SX_ERR_INVALID, "the callable does not compile (%s): %s", nv.error_string(r), log.c_str());
+    }
+    size_t bytes = 0;
+    nv.cubin_size(prog, &bytes);
+    std::vector<char> cubin(bytes);
+    nv.cubin(prog, cubin.data());
+    nv.destroy(&prog);
+    Compiled c;
+    cudaError_t e = cudaLibraryLoadData(&c.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&c.kernel, c.lib, "sx_user_map");
+    if (e != cudaSuccess) {
+        if (c.lib) cudaLibraryUnload(c.lib);
+        return cuda_fail(e, "loading the compiled callable");
+    }
+    if (g_jit.size() >= kMaxCompiled) {
+        // make room: a kernel still running may belong to any entry, so wait for the device
+        cudaDeviceSynchronize();
+        for (auto &kv : g_jit) cudaLibraryUnload(kv.second.lib);
+        g_jit.clear();
+    }
+    g_jit.emplace(key, c);
+    *out = c.kernel;
+    return SX_OK;
+}
+
+}  // namespace
+}  // namespace sx
+
+using namespace sx;
+
+extern "C" int sx_transform_src(sx_executor *e, const char *src, const sx_array *in, sx_array *out) {
+    TraceRange tr("sx_transform_src");
+    if (!e || !src || !in || !out) return fail(SX_ERR_INVALID, "NULL argument");
+    if (in->t != e->t || out->t != e->t) return fail(SX_ERR_INVALID, "arrays must be placed on the executor's target");
+    if (in->dtype != out->dtype) return fail(SX_ERR_DTYPE, "input and output differ in type");
+    if (!type_name(in->dtype)) return fail(SX_ERR_DTYPE, "unknown dtype %d", in->dtype);
+    if (in->n != out->n) return fail(SX_ERR_INVALID, "input and output differ in length");
+    const size_t bytes = in->n * dtype_size(in->dtype);
+    const uintptr_t pi = (uintptr_t)in->ptr, po = (uintptr_t)out->ptr;
+    if (pi != po && bytes && pi < po + bytes && po < pi + bytes)
+        return fail(SX_ERR_OVERLAP, "output partially overlaps the input");
+    DeviceScope ds(e->t->device);
+    cudaKernel_t k = nullptr;
+    SX_TRY(get_kernel(e->t, in->dtype, src, &k));
+    if (in->n) {
+        const void *pin = in->ptr;
+        void *pout = out->ptr;
+        unsigned long long n = in->n;
+        void *args[] = {(void *)&pin, (void *)&pout, (void *)&n};
+        uint64_t blocks = (in->n + 255) / 256;
+        const uint64_t cap = (uint64_t)e->t->sm_count * 8;
+        if (blocks > cap) blocks = cap;
+        SX_CUDA(cudaLaunchKernel((const void *)k, dim3((unsigned)blocks), dim3(256), args, 0, e->t->stream));
+    }
+    if (e->policy == SX_PAR) {
+        SX_CUDA(cudaStreamSynchronize(e->t->stream));
+        return check_device_error(e->t);
+    }
+    return SX_OK;
+}

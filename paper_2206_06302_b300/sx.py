@@ -148,6 +148,7 @@ _PROTOS = {
     "sx_stream_fused": [P, P, P, P, D, I],
     "sx_stream_host": [P, P, P, P, P, P, P, D, I],
     "sx_transform_u8": [P, I, P, P],
+    "sx_transform_src": [P, C.c_char_p, P, P],
     "sx_batch_create": [P, C.POINTER(sx_batch_item), SZ, C.POINTER(sx_batch_cfg), PP],
     "sx_batch_launch": [P],
     "sx_batch_launch_async": [P, PP],
@@ -404,6 +405,11 @@ def sx_stream_host(e, ha: int, hb: int, hc: int, a, b, c, q: float = 3.0, iters:
 
 def sx_transform_u8(e, fn: int, x, out) -> None:
     _check(lib.sx_transform_u8(e, fn, x, out), "sx_transform_u8")
+
+
+def sx_transform_src(e, src: str, x, out) -> None:
+    """out[i] = sx_fn(x[i]) with sx_fn defined by the CUDA C++ source `src` (compiled at run time)."""
+    _check(lib.sx_transform_src(e, src.encode(), x, out), "sx_transform_src")
 
 
 def sx_batch_create(t, items, cfg=None):

@@ -678,3 +678,44 @@ def test_target_on_torchs_default_stream_is_ordered_with_torch():
         sx.sx_free(w)
     sx.sx_executor_destroy(e)
     sx.sx_target_destroy(t)
+
+
+UPPER_SRC = """
+__device__ sx_t sx_fn(sx_t c) {
+    return (c >= 'a' && c <= 'z') ? (sx_t)(c - ('a' - 'A')) : c;
+}
+"""
+
+
+def test_transform_with_a_callable_given_as_source(target, executor):
+    """Any device callable (Section 4.2), compiled at run time: Listing 3's to_upper given as
+    source equals the oracle's; binary64 and binary32 expressions round each operation once
+    (no contraction), in place as well; the compiled callable is reused; a callable that does not
+    compile is refused with the compiler's message."""
+    text = np.frombuffer(b"hello, world " + bytes(range(256)) * 13 + b"tail", np.uint8).copy()
+    ds, do = to_device(target, text), empty(target, np.uint8, text.size)
+    for _ in range(2):  # the second call takes the compiled callable from the cache
+        sx.sx_transform_src(executor, UPPER_SRC, ds, do)
+        assert_bitwise(to_host(do), oracle.to_upper(text), "to_upper from source")
+    for h in (ds, do):
+        sx.sx_free(h)
+    n = 100003
+    x64 = _inputs(n, np.float64, 21)[0]
+    dx = to_device(target, x64)
+    do = empty(target, np.float64, n)
+    sx.sx_transform_src(executor, "__device__ sx_t sx_fn(sx_t x) { return x * 2.5 + 1.0; }", dx, do)
+    assert_bitwise(to_host(do), np.add(np.multiply(x64, 2.5), 1.0), "binary64 x*2.5+1")
+    sx.sx_transform_src(executor, "__device__ sx_t sx_fn(sx_t x) { return x * x; }", dx, dx)  # in place
+    assert_bitwise(to_host(dx), np.multiply(x64, x64), "binary64 x*x in place")
+    for h in (dx, do):
+        sx.sx_free(h)
+    x32 = _inputs(n, np.float32, 22)[0]
+    dx, do = to_device(target, x32), empty(target, np.float32, n)
+    sx.sx_transform_src(executor, "__device__ sx_t sx_fn(sx_t x) { return x * x - 0.5f; }", dx, do)
+    want = np.subtract(np.multiply(x32, x32, dtype=np.float32), np.float32(0.5), dtype=np.float32)
+    assert_bitwise(to_host(do), want, "binary32 x*x-0.5")
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_transform_src(executor, "__device__ sx_t sx_fn(sx_t x) { return undefined_name; }", dx, do)
+    assert ei.value.status == sx.SX_ERR_INVALID and "undefined_name" in str(ei.value)
+    for h in (dx, do):
+        sx.sx_free(h)
