@@ -114,3 +114,24 @@ def test_header_is_plain_c_and_links(tmp_path):
         pytest.skip("a GPU is present: the GPU test runs the client")
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 2 and "no device" in r.stderr, (r.returncode, r.stderr)
+
+
+def build_cpp_client(tmp_path):
+    """Compile and link tests/cpp_api_program.cpp (the header-only C++ layer sx.hpp) against libsx."""
+    lib = _builder().build()
+    exe = str(tmp_path / "cpp_api_program")
+    cmd = ["g++", "-std=c++17", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "cpp_api_program.cpp"), "-o", exe, "-L", os.path.dirname(lib), "-lsx",
+           "-Wl,-rpath," + os.path.dirname(lib)]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    return exe
+
+
+def test_cpp_layer_compiles_and_links(tmp_path):
+    """sx.hpp compiles as strict C++17 and a client links; without a device it exits 2."""
+    import torch
+    exe = build_cpp_client(tmp_path)
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the GPU test runs the client")
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 2 and "no device" in r.stderr, (r.returncode, r.stderr)

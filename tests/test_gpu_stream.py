@@ -719,3 +719,12 @@ def test_transform_with_a_callable_given_as_source(target, executor):
     assert ei.value.status == sx.SX_ERR_INVALID and "undefined_name" in str(ei.value)
     for h in (dx, do):
         sx.sx_free(h)
+
+
+def test_cpp_layer_closed_form(tmp_path):
+    """The header-only C++ layer (include/sx.hpp): STREAM as algorithm calls under par.on(exec)
+    on allocator-placed vectors, then the library's pass loop, reaches the closed form exactly."""
+    import subprocess
+    from test_abi import build_cpp_client
+    r = subprocess.run([build_cpp_client(tmp_path)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "closed form ok" in r.stdout, (r.returncode, r.stdout, r.stderr)
