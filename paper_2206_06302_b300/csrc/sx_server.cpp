@@ -485,15 +485,20 @@ void server_loop(sx_server *s) {
         const uint64_t seen = s->arrivals.load(std::memory_order_acquire);
         if (!s->inflight.empty()) {
             // GPU busy: wait for the oldest step without the lock; come back early for arrivals
-            // or freed memory (admission), and let callers that want the lock have it
+            // or freed memory (admission), and let callers that want the lock have it.  The first
+            // 500 us are spent polling (a step usually takes ~100 us); after that the thread sleeps
+            // between polls, so that long steps do not keep a core busy.
             Step &front = s->inflight.front();
             const bool by_word = front.slot >= 0;
             const uint64_t want = front.seq;
             cudaEvent_t ev = front.ev;
             lk.unlock();
+            const double spin_until = now_seconds() + 5e-4;
             while (!(by_word ? step_reported(s, want) : cudaEventQuery(ev) != cudaErrorNotReady) &&
-                   s->arrivals.load(std::memory_order_acquire) == seen)
-                std::this_thread::yield();
+                   s->arrivals.load(std::memory_order_acquire) == seen) {
+                if (now_seconds() < spin_until) std::this_thread::yield();
+                else std::this_thread::sleep_for(std::chrono::microseconds(20));
+            }
             wait_contenders();
             lk.lock();
         } else {
