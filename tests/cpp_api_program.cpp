@@ -45,6 +45,18 @@ int main() {
                     return 1;
                 }
         }
+        // a failed call throws sx::error with the library's status
+        sx::vector<double> shorter(n - 1, alloc);
+        try {
+            sx::copy(sx::par.on(exec), a, shorter);
+            std::fprintf(stderr, "copy between lengths %zu and %zu did not throw\n", n, n - 1);
+            return 1;
+        } catch (const sx::error &e) {
+            if (e.status() != SX_ERR_INVALID) {
+                std::fprintf(stderr, "unexpected status %d: %s\n", e.status(), e.what());
+                return 1;
+            }
+        }
         std::printf("closed form ok through sx.hpp: a = %.0f after 10 passes\n", want[0]);
         return 0;
     } catch (const sx::error &e) {
