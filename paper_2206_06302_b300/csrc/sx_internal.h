@@ -173,6 +173,7 @@ int launch_stream_op(const sx_target *t, cudaStream_t stream, int op, int dtype,
 int launch_fill(cudaStream_t stream, int dtype, void *out, size_t n, double value);
 int launch_seed(cudaStream_t stream, int dtype, void *out, size_t n, uint64_t seed, double lo,
                 double hi, uint64_t index_base);
+// fp64_mul < 0: the product unit is chosen by the elements per SM
 int launch_stream_fused(const sx_target *t, cudaStream_t stream, int dtype, void *a, void *b,
                         void *c, size_t n, double q, int iters, int fp64_mul);
 int launch_u8_transform(const sx_target *t, cudaStream_t stream, int fn, const void *in,

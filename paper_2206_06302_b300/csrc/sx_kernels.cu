@@ -33,6 +33,12 @@ k_stream_vec(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t
     constexpr int EPV = VB / (int)sizeof(T);
     constexpr bool HAS_Y = (OP == SX_OP_ADD || OP == SX_OP_TRIAD);
 
+    // Launched as a programmatic dependent of the kernel before it on the stream: wait until
+    // that kernel has completed and its stores are visible (at once otherwise), then allow the
+    // next kernel's blocks to be scheduled, so that its launch overlaps this kernel's tail.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t body_end = head + nvec * EPV;
     if (gtid < head + (n - body_end)) {
@@ -86,40 +92,56 @@ struct VecLaunch {
     unsigned blocks, threads;
     cudaStream_t s;
     uint64_t n, head, nvec;
+    bool pdl;  // launch as a programmatic dependent of the stream's previous kernel
 };
 
+// Launches one k_stream_vec instantiation with the shape of `l`.
+template <int OP, class T, int VB, int U, int HINT, int MM>
+cudaError_t launch_vec_one(const VecLaunch &l, const T *x, const T *y, T *out, T q) {
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(l.blocks);
+    lc.blockDim = dim3(l.threads);
+    lc.stream = l.s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = l.pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&lc, k_stream_vec<OP, T, VB, U, HINT, MM>, x, y, out, l.n, l.head, l.nvec, q);
+}
+
 template <int OP, class T, int VB, int U, int HINT>
-void launch_vec_mm(int mm, const VecLaunch &l, const T *x, const T *y, T *out, T q) {
+cudaError_t launch_vec_mm(int mm, const VecLaunch &l, const T *x, const T *y, T *out, T q) {
     // the product unit only matters for binary64 SCALE and TRIAD
     // (aliased outputs, HINT 2, keep the FP64 pipe: a rare case not worth more instantiations)
     constexpr bool MUL64 = sizeof(T) == 8 && (OP == SX_OP_SCALE || OP == SX_OP_TRIAD) && HINT != 2;
     if constexpr (MUL64) {
         switch (mm) {
-            case 1: k_stream_vec<OP, T, VB, U, HINT, 1><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q); return;
-            case 2: k_stream_vec<OP, T, VB, U, HINT, 2><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q); return;
-            case 3: k_stream_vec<OP, T, VB, U, HINT, 3><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q); return;
-            case 4: k_stream_vec<OP, T, VB, U, HINT, 4><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q); return;
+            case 1: return launch_vec_one<OP, T, VB, U, HINT, 1>(l, x, y, out, q);
+            case 2: return launch_vec_one<OP, T, VB, U, HINT, 2>(l, x, y, out, q);
+            case 3: return launch_vec_one<OP, T, VB, U, HINT, 3>(l, x, y, out, q);
+            case 4: return launch_vec_one<OP, T, VB, U, HINT, 4>(l, x, y, out, q);
             default: break;
         }
     }
-    k_stream_vec<OP, T, VB, U, HINT, 0><<<l.blocks, l.threads, 0, l.s>>>(x, y, out, l.n, l.head, l.nvec, q);
+    return launch_vec_one<OP, T, VB, U, HINT, 0>(l, x, y, out, q);
 }
 
 template <int OP, class T, int VB, int U>
-void launch_vec_hint(int hint, int mm, const VecLaunch &l, const T *x, const T *y, T *out, T q) {
+cudaError_t launch_vec_hint(int hint, int mm, const VecLaunch &l, const T *x, const T *y, T *out, T q) {
     switch (hint) {
-        case 0: launch_vec_mm<OP, T, VB, U, 0>(mm, l, x, y, out, q); break;
-        case 1: launch_vec_mm<OP, T, VB, U, 1>(mm, l, x, y, out, q); break;
-        default: launch_vec_mm<OP, T, VB, U, 2>(mm, l, x, y, out, q); break;
+        case 0: return launch_vec_mm<OP, T, VB, U, 0>(mm, l, x, y, out, q);
+        case 1: return launch_vec_mm<OP, T, VB, U, 1>(mm, l, x, y, out, q);
+        default: return launch_vec_mm<OP, T, VB, U, 2>(mm, l, x, y, out, q);
     }
 }
 
 template <int OP, class T, int VB>
-void launch_vec_unroll(int unroll, int hint, int mm, const VecLaunch &l, const T *x, const T *y, T *out, T q) {
+cudaError_t launch_vec_unroll(int unroll, int hint, int mm, const VecLaunch &l, const T *x, const T *y, T *out, T q) {
     switch (unroll) {
-        case 1: launch_vec_hint<OP, T, VB, 1>(hint, mm, l, x, y, out, q); break;
-        case 2: launch_vec_hint<OP, T, VB, 2>(hint, mm, l, x, y, out, q); break;
-        default: launch_vec_hint<OP, T, VB, 4>(hint, mm, l, x, y, out, q); break;
+        case 1: return launch_vec_hint<OP, T, VB, 1>(hint, mm, l, x, y, out, q);
+        case 2: return launch_vec_hint<OP, T, VB, 2>(hint, mm, l, x, y, out, q);
+        default: return launch_vec_hint<OP, T, VB, 4>(hint, mm, l, x, y, out, q);
     }
 }
 
@@ -165,14 +187,18 @@ int launch_vector(const sx_target *t, cudaStream_t s, const T *x, const T *y, T 
     if (blocks < edge_blocks) blocks = edge_blocks;
     if (blocks == 0) blocks = 1;
     if (blocks > 0x7fffffffull) return fail(SX_ERR_INVALID, "grid too large (%llu blocks)", (unsigned long long)blocks);
-    const VecLaunch l{(unsigned)blocks, threads, s, n, head, nvec};
+    // programmatic dependent launch on the library's and callers' streams; the default streams
+    // keep plain serialisation
+    const bool pdl = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+    const VecLaunch l{(unsigned)blocks, threads, s, n, head, nvec, pdl};
     const int mm = mul_variant(c.fp64_mul, (double)q);
-    if (VB == 16)
-        launch_vec_unroll<OP, T, 16>(c.unroll, hint, mm, l, x, y, out, q);
-    else
-        launch_vec_unroll<OP, T, 32>(c.unroll, hint, mm, l, x, y, out, q);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "k_stream_vec launch");
+    cudaError_t e = VB == 16 ? launch_vec_unroll<OP, T, 16>(c.unroll, hint, mm, l, x, y, out, q)
+                             : launch_vec_unroll<OP, T, 32>(c.unroll, hint, mm, l, x, y, out, q);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "k_stream_vec launch");
+    }
     return SX_OK;
 }
 
@@ -226,13 +252,16 @@ unsigned setup_blocks(size_t n) {
 // per element from one read of a and write a, b, c once, bit-identical to four launches per
 // pass.
 template <int MM, class T>
+__device__ __forceinline__ void fused_pass(T &a, T &b, T &c, T q, int lane) {
+    c = a;
+    b = mul_sel<MM>(c, q, lane);
+    c = add_rn(a, b);
+    a = add_rn(b, mul_sel<MM>(c, q, lane + 1));
+}
+
+template <int MM, class T>
 __device__ __forceinline__ void fused_chain(T &a, T &b, T &c, T q, int iters, int lane) {
-    for (int k = 0; k < iters; ++k) {
-        c = a;
-        b = mul_sel<MM>(c, q, lane);
-        c = add_rn(a, b);
-        a = add_rn(b, mul_sel<MM>(c, q, lane + 1));
-    }
+    for (int k = 0; k < iters; ++k) fused_pass<MM>(a, b, c, q, lane);
 }
 
 template <class T, int MM>
@@ -400,32 +429,54 @@ int launch_stream_fused(const sx_target *t, cudaStream_t s, int dtype, void *a, 
                         size_t n, double q, int iters, int mm) {
     if (n == 0 || iters <= 0) return SX_OK;
     const size_t es = dtype_size(dtype);
+    const uint64_t sms = (uint64_t)t->sm_count;
+    double *a8 = (double *)a, *b8 = (double *)b, *c8 = (double *)c;
+    if (dtype == SX_F64 && n <= 1024 * sms) {
+        // Few elements per SM: the time is that of each warp's chain of dependent operations.
+        // On B300 a dependent FP64 add or multiply takes ~80 cycles and an SM sub-partition's
+        // FP64 unit ~64 cycles per warp instruction, so one element per thread in blocks of two
+        // warps spreads the chains over as many sub-partitions as there are warps; up to one
+        // warp per sub-partition the products stay on the FP64 pipe (the integer-unit product
+        // has the longer dependent latency), beyond that they move to the integer units.
+        if (mm < 0) mm = n <= 128 * sms ? 0 : 1;
+        const int v = mul_variant(mm, q);
+        const unsigned threads = 64;
+        const unsigned g = (unsigned)((n + threads - 1) / threads);
+        if (v == 1 || v == 2) k_stream_fused<double, 1><<<g, threads, 0, s>>>(a8, b8, c8, n, q, iters);
+        else if (v == 3 || v == 4) k_stream_fused<double, 3><<<g, threads, 0, s>>>(a8, b8, c8, n, q, iters);
+        else k_stream_fused<double, 0><<<g, threads, 0, s>>>(a8, b8, c8, n, q, iters);
+        SX_CUDA(cudaGetLastError());
+        return SX_OK;
+    }
+    if (mm < 0) mm = 1;  // many elements per SM: the products go to the integer units
     const bool aligned = ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0) &&
                          ((uintptr_t)c % 16 == 0) && ((n * es) % 16 == 0);
-    const uint64_t cap = (uint64_t)t->sm_count * 8;
+    const uint64_t cap = sms * 8;
     const int v = dtype == SX_F64 ? mul_variant(mm, q) : 0;
-    double *a8 = (double *)a, *b8 = (double *)b, *c8 = (double *)c;
+    // Each thread's chains are arithmetic (the FP64 pipe and the integer units), so small arrays
+    // are spread over as many SMs as possible: blocks shrink from 256 to 32 threads until the
+    // grid has a block per SM.
+    const uint64_t units = aligned ? n * es / 16 : n;
+    unsigned threads = 256;
+    while (threads > 32 && (units + threads - 1) / threads < sms) threads /= 2;
+    uint64_t blocks = (units + threads - 1) / threads;
+    if (blocks > cap) blocks = cap;
+    const unsigned g = (unsigned)blocks;
     if (aligned) {
-        const uint64_t nvec = n * es / 16;
-        uint64_t blocks = (nvec + 255) / 256;
-        if (blocks > cap) blocks = cap;
-        const unsigned g = (unsigned)blocks;
+        const uint64_t nvec = units;
         if (dtype == SX_F32)
-            k_stream_fused_v<float, 0><<<g, 256, 0, s>>>((float *)a, (float *)b, (float *)c, nvec, (float)q, iters);
-        else if (v == 1) k_stream_fused_v<double, 1><<<g, 256, 0, s>>>(a8, b8, c8, nvec, q, iters);
-        else if (v == 2) k_stream_fused_v<double, 2><<<g, 256, 0, s>>>(a8, b8, c8, nvec, q, iters);
-        else if (v == 3) k_stream_fused_v<double, 3><<<g, 256, 0, s>>>(a8, b8, c8, nvec, q, iters);
-        else if (v == 4) k_stream_fused_v<double, 4><<<g, 256, 0, s>>>(a8, b8, c8, nvec, q, iters);
-        else k_stream_fused_v<double, 0><<<g, 256, 0, s>>>(a8, b8, c8, nvec, q, iters);
+            k_stream_fused_v<float, 0><<<g, threads, 0, s>>>((float *)a, (float *)b, (float *)c, nvec, (float)q, iters);
+        else if (v == 1) k_stream_fused_v<double, 1><<<g, threads, 0, s>>>(a8, b8, c8, nvec, q, iters);
+        else if (v == 2) k_stream_fused_v<double, 2><<<g, threads, 0, s>>>(a8, b8, c8, nvec, q, iters);
+        else if (v == 3) k_stream_fused_v<double, 3><<<g, threads, 0, s>>>(a8, b8, c8, nvec, q, iters);
+        else if (v == 4) k_stream_fused_v<double, 4><<<g, threads, 0, s>>>(a8, b8, c8, nvec, q, iters);
+        else k_stream_fused_v<double, 0><<<g, threads, 0, s>>>(a8, b8, c8, nvec, q, iters);
     } else {
-        uint64_t blocks = (n + 255) / 256;
-        if (blocks > cap) blocks = cap;
-        const unsigned g = (unsigned)blocks;
         if (dtype == SX_F32)
-            k_stream_fused<float, 0><<<g, 256, 0, s>>>((float *)a, (float *)b, (float *)c, n, (float)q, iters);
-        else if (v == 1 || v == 2) k_stream_fused<double, 1><<<g, 256, 0, s>>>(a8, b8, c8, n, q, iters);
-        else if (v == 3 || v == 4) k_stream_fused<double, 3><<<g, 256, 0, s>>>(a8, b8, c8, n, q, iters);
-        else k_stream_fused<double, 0><<<g, 256, 0, s>>>(a8, b8, c8, n, q, iters);
+            k_stream_fused<float, 0><<<g, threads, 0, s>>>((float *)a, (float *)b, (float *)c, n, (float)q, iters);
+        else if (v == 1 || v == 2) k_stream_fused<double, 1><<<g, threads, 0, s>>>(a8, b8, c8, n, q, iters);
+        else if (v == 3 || v == 4) k_stream_fused<double, 3><<<g, threads, 0, s>>>(a8, b8, c8, n, q, iters);
+        else k_stream_fused<double, 0><<<g, threads, 0, s>>>(a8, b8, c8, n, q, iters);
     }
     SX_CUDA(cudaGetLastError());
     return SX_OK;

@@ -669,9 +669,10 @@ int sx_stream_fused(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, doubl
     TraceRange tr("sx_stream_fused");
     SX_TRY(check_stream_arrays(e, a, b, c, iters));
     DeviceScope ds(e->t->device);
-    // the chain is four binary64 operations per pass, two of them products: by default the
-    // products go to the integer units (bit-identical), unless the executor fixes fp64_mul
-    const int mm = e->fixed_cfg ? e->cfg.fp64_mul : 1;
+    // the chain is four binary64 operations per pass, two of them products: unless the executor
+    // fixes fp64_mul, the launch picks the unit (FP64 pipe for few elements per SM, the integer
+    // units otherwise; bit-identical either way)
+    const int mm = e->fixed_cfg ? e->cfg.fp64_mul : -1;
     SX_TRY(launch_stream_fused(e->t, e->t->stream, a->dtype, a->ptr, b->ptr, c->ptr, a->n, q, iters, mm));
     return finish_call(e);
 }

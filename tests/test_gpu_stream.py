@@ -522,6 +522,18 @@ def test_fused_product_units(target, mm):
     sx.sx_executor_destroy(e)
 
 
+@pytest.mark.parametrize("n", [1, 63, 1000, 18944, 18945, 40001, 151552, 151553])
+def test_fused_launch_shapes_by_size(target, executor, n):
+    """The fused kernel's launch shape and default product unit change with the elements per SM
+    (one element per thread and the FP64 pipe up to 128 per SM, the integer units up to 1024 per
+    SM, vectors beyond); every shape gives the oracle's bits, around each boundary (148 SMs)."""
+    a, b, c = si.stream_arrays(n, np.float64, base_seed=9)
+    ga, gb, gc = _stream_device(target, executor, a, b, c, 3.0, 9, fused=True)
+    oracle.stream(a, b, c, 3.0, 9)
+    for g, w, name in ((ga, a, "a"), (gb, b, "b"), (gc, c, "c")):
+        assert_bitwise(g, w, f"{name}, n={n}")
+
+
 def test_device_failure_path_selftest():
     """A kernel's bounded wait that runs out reports SX_ERR_DEVICE at the next synchronisation
     and leaves the context usable (no trap, no hang: the wait is limited to 2 ms)."""
@@ -676,6 +688,47 @@ def test_target_on_torchs_default_stream_is_ordered_with_torch():
     assert_bitwise(got, oracle.triad(hx.numpy(), hy.numpy(), 3.0), "ordered with torch")
     for w in (wx, wy, wo):
         sx.sx_free(w)
+    sx.sx_executor_destroy(e)
+    sx.sx_target_destroy(t)
+
+
+def test_programmatic_launches_keep_order_with_torch_kernels():
+    """Each VECTOR kernel is launched as a programmatic dependent of the kernel before it on the
+    stream.  A chain on one non-default stream that alternates library kernels (scale, triad,
+    copy, add) with torch kernels, every step reading what the step before wrote, gives the
+    serial result bit for bit, for one-block, multi-block and multi-wave arrays."""
+    import torch
+    import paper_2206_06302_b300 as pkg
+    s = torch.cuda.Stream()
+    t = pkg.target_on_torch_stream(0, s)
+    e = sx.sx_executor_create(t, sx.SX_PAR_TASK)
+    for n in (1000, 65537, (1 << 22) + 3):
+        hx = si.uniform(si.array_seed(4242, 0, n), n, np.float64)
+        with torch.cuda.stream(s):
+            x = torch.from_numpy(hx).to("cuda", non_blocking=False)
+            y, z = torch.empty_like(x), torch.empty_like(x)
+            wx, wy, wz = (pkg.wrap_tensor(t, v) for v in (x, y, z))
+            rx = hx.copy()
+            for _ in range(12):
+                sx.sx_execute_async(e, sx.SX_OP_SCALE, wx, None, wy, 3.0, future=False)  # y = 3x
+                torch.sub(y, 1.0, out=x)                                                # x = y - 1
+                sx.sx_execute_async(e, sx.SX_OP_TRIAD, wx, wy, wz, 3.0, future=False)  # z = x + 3y
+                torch.mul(z, 0.25, out=x)                                               # x = z / 4
+                sx.sx_execute_async(e, sx.SX_OP_COPY, wx, None, wy, 0.0, future=False)  # y = x
+                sx.sx_execute_async(e, sx.SX_OP_ADD, wx, wy, wz, 0.0, future=False)     # z = x + y
+                torch.sub(z, y, out=x)                                                  # x = z - y
+                ry = oracle.scale(rx, 3.0)
+                rx = ry - 1.0
+                rz = oracle.triad(rx, ry, 3.0)
+                rx = rz * 0.25
+                ry = oracle.copy(rx)
+                rz = oracle.add(rx, ry)
+                rx = rz - ry
+            got = [v.cpu().numpy() for v in (x, y, z)]
+        for g, w, name in zip(got, (rx, ry, rz), "xyz"):
+            assert_bitwise(g, w, f"{name}, n={n}")
+        for w in (wx, wy, wz):
+            sx.sx_free(w)
     sx.sx_executor_destroy(e)
     sx.sx_target_destroy(t)
 
