@@ -44,10 +44,10 @@ RESEED_EVERY = 100
 # dram__bytes_read.sum + dram__bytes_write.sum of one Triad launch (FP64, n = 2^27) from an ncu
 # capture, with the sha256 of the kernel source it was taken on; reported as null when the
 # source has changed since.
-NCU_TRAFFIC = {"kernel": "k_stream_vec<3, double, 32, 1, 1, 4>", "n": 1 << 27,
-               "bytes": 4 * 768897536,  # captured at n = 2^25 (536945664 read + 231951872 written), x4
-               "cfg": {"variant": 1, "vec_bytes": 32, "unroll": 1, "cache_hint": 1, "fp64_mul": 2},
-               "source_sha256": "db28c81ab1aac2727a69a4082afd6767d8e3cbfe09cfb3e1bebabf9d3069c20b"}
+NCU_TRAFFIC = {"kernel": "k_stream_vec<3, double, 32, 2, 0, 4>", "n": 1 << 27,
+               "bytes": 4 * 770115840,  # captured at n = 2^25 (536900096 read + 233215744 written), x4
+               "cfg": {"variant": 1, "vec_bytes": 32, "unroll": 2, "cache_hint": 0, "fp64_mul": 2},
+               "source_sha256": "157f39571f52ee086f5e8c06c0fc7aba3945e11d1112e94fcbb0c60509707e25"}
 
 
 def _rank_env():
@@ -396,9 +396,9 @@ def served_workload(sx, seed, count):
 
 def served_section(sx, torch, t, stream, args, rank):
     """Poisson stream of copy/scale/add/triad requests (FP64/FP32), n log-uniform in
-    [2^12, 2^28], inputs constructed on the device, 64 GB arena.  First both modes at
-    saturation (every request at t=0); the per-call FIFO's saturation throughput is the
-    measured single-stream capacity.  Then continuous batching vs the per-call FIFO at offered
+    [2^12, 2^28], inputs constructed on the device, 64 GB arena.  After an untimed warm-up,
+    both modes at saturation (every request at t=0; best of two runs each); the per-call FIFO's
+    saturation throughput is the measured single-stream capacity.  Then continuous batching vs the per-call FIFO at offered
     loads of 0.5, 0.8 and 0.95 of that capacity: p50/p99 latency (submission to completion seen
     by the server), the p99 of the shorter half of the requests, and throughput."""
     import stream_inputs as si
@@ -413,11 +413,19 @@ def served_section(sx, torch, t, stream, args, rank):
                        f"device, {args.serve_budget_gb:g} GB arena, mean {mean_bytes / 1e6:.1f} MB "
                        f"moved per request", "saturation_GB/s": {}, "runs": []}
     zero = [0.0] * len(work)
-    for mode, name in modes:
-        _, stats, span = serve_run(sx, t, work, zero, budget, mode)
-        out["saturation_GB/s"][name] = round(stats["bytes_moved"] / span / 1e9, 1)
-        out.setdefault("saturation_frac_measured", {})[name] = round(
-            stats["bytes_moved"] / span / 1e9 / _measured_peaks()[0], 4)
+    # untimed warm-up of both modes (the first server of a process starts cold), then each mode
+    # at saturation twice, alternating; the better run of each is its saturation throughput
+    for mode, _ in modes:
+        serve_run(sx, t, work[:200], zero[:200], budget, mode)
+    sat = {name: [] for _, name in modes}
+    for _ in range(2):
+        for mode, name in modes:
+            _, stats, span = serve_run(sx, t, work, zero, budget, mode)
+            sat[name].append(stats["bytes_moved"] / span / 1e9)
+    for name, runs in sat.items():
+        out["saturation_GB/s"][name] = round(max(runs), 1)
+        out.setdefault("saturation_runs_GB/s", {})[name] = [round(v, 1) for v in runs]
+        out.setdefault("saturation_frac_measured", {})[name] = round(max(runs) / _measured_peaks()[0], 4)
     capacity = out["saturation_GB/s"]["fifo"] * 1e9
     out["capacity_from"] = "per-call FIFO throughput at saturation"
     for load in [float(v) for v in args.serve_loads.split(",") if v]:
@@ -687,7 +695,8 @@ def cpu_oracle_threads_gbs(n: int, seconds: float):
 
 def run_sweep(args):
     """Size sweep (the paper's array-size figure): n = 2^lo..2^hi per array, FP64 and FP32, the
-    four kernels, VECTOR vs BULK (TMA bulk-copy staging) at fixed launch shapes.  Prints one
+    four kernels, VECTOR vs BULK (TMA bulk-copy staging of the inputs) vs TMA (bulk copies both
+    ways) at fixed launch shapes.  Prints one
     JSON line.  Back-to-back launches on the same arrays: below ~2^22-2^23 elements the three
     arrays stay in the 126 MB L2."""
     import torch
@@ -699,6 +708,8 @@ def run_sweep(args):
         "vector": dict(variant=sx.SX_VARIANT_VECTOR, threads=256, vec_bytes=32, unroll=2, fp64_mul=2),
         "bulk": dict(variant=sx.SX_VARIANT_BULK, threads=256, blocks_per_sm=2, tile_bytes=16384,
                      stages=3, fp64_mul=2),
+        "tma": dict(variant=sx.SX_VARIANT_TMA, threads=256, blocks_per_sm=2, tile_bytes=16384,
+                    stages=3, fp64_mul=2),
     }
     execs = {k: sx.sx_executor_create(t, sx.SX_PAR_TASK, v) for k, v in shapes.items()}
     ops = (("copy", sx.SX_OP_COPY, 2), ("scale", sx.SX_OP_SCALE, 2), ("add", sx.SX_OP_ADD, 3),
@@ -769,7 +780,8 @@ def run_ours(args):
                     sx.sx_tune(t, op, dcode, tune_n)
         if args.tune_cache:
             sx.sx_tune_save(args.tune_cache)
-    forced = {"vector": dict(variant=sx.SX_VARIANT_VECTOR), "bulk": dict(variant=sx.SX_VARIANT_BULK)}
+    forced = {"vector": dict(variant=sx.SX_VARIANT_VECTOR), "bulk": dict(variant=sx.SX_VARIANT_BULK),
+              "tma": dict(variant=sx.SX_VARIANT_TMA)}
     e_auto = sx.sx_executor_create(t, sx.SX_PAR_TASK, forced.get(args.variant))
     execs = {}  # per dtype and op: an executor fixed to the shape resolved at tune_n
     for dcode, dname in ((sx.SX_F64, "f64"), (sx.SX_F32, "f32")):
@@ -967,10 +979,10 @@ def main(argv=None):
                     help="seeded uniform [-1,1) inputs, or a=1, b=2, c=0")
     ap.add_argument("--stream-doubling", action="store_true",
                     help="double a once after construction, as classic STREAM does before timing")
-    ap.add_argument("--variant", choices=["auto", "vector", "bulk"], default="auto",
+    ap.add_argument("--variant", choices=["auto", "vector", "bulk", "tma"], default="auto",
                     help="kernel family of the timed passes (auto: the tuner table)")
     ap.add_argument("--sweep", action="store_true",
-                    help="instead of the step benchmark: the size sweep, vector vs TMA bulk staging")
+                    help="instead of the step benchmark: the size sweep, vector vs the two TMA bulk-copy families")
     ap.add_argument("--sweep-lo", type=int, default=10)
     ap.add_argument("--sweep-hi", type=int, default=29)
     ap.add_argument("--ref-n", type=int, default=1 << 22)

@@ -83,19 +83,26 @@ typedef enum sx_policy { SX_PAR = 1, SX_PAR_TASK = 2 } sx_policy;
  * with the Tensor Memory Accelerator's bulk copies (a producer warp issues cp.async.bulk
  * global->shared per pipeline stage; consumer warps compute from shared memory and store to
  * global memory).
+ * TMA: the BULK pipeline with the results written back by bulk copies as well: consumer warps
+ * compute each tile in place in shared memory and a storer warp issues one cp.async.bulk
+ * shared->global per tile (copy: the storer takes each tile as it arrives, no consumer work).
  * AUTO: the autotuner's choice for (op, dtype, size) if it has one, else a fixed default. */
-typedef enum sx_variant { SX_VARIANT_AUTO = 0, SX_VARIANT_VECTOR = 1, SX_VARIANT_BULK = 2 } sx_variant;
+typedef enum sx_variant {
+    SX_VARIANT_AUTO = 0, SX_VARIANT_VECTOR = 1, SX_VARIANT_BULK = 2, SX_VARIANT_TMA = 3
+} sx_variant;
 
 /* Launch configuration of one algorithm call.  A zero field means "default".
- *   threads        threads per block (multiple of 32; VECTOR: 32..1024; BULK: 64..1024, one producer warp)
+ *   threads        threads per block (multiple of 32; VECTOR: 32..1024; BULK: 64..1024, a producer
+ *                  warp and consumer warps; TMA: 96..1024, a producer warp, a storer warp and
+ *                  consumer warps, which copy leaves idle)
  *   blocks_per_sm  VECTOR: grid = SMs * blocks_per_sm with a grid-stride loop; 0 = one tile
- *                  per block (grid covers the array).  BULK: persistent blocks per SM (1..4)
+ *                  per block (grid covers the array).  BULK, TMA: persistent blocks per SM (1..4)
  *   vec_bytes      VECTOR: 16 or 32 bytes per thread access
  *   unroll         VECTOR: vector accesses per thread per tile (1, 2 or 4)
  *   cache_hint     VECTOR: 0 = default caching, 1 = streaming (L1 no-allocate loads with an
  *                  L2 256-byte prefetch hint, evict-first stores)
- *   tile_bytes     BULK: bytes per array per pipeline stage (multiple of 1024, 1024..65536)
- *   stages         BULK: pipeline depth (2..8); shared memory = stages*tile_bytes*inputs
+ *   tile_bytes     BULK, TMA: bytes per array per pipeline stage (multiple of 1024, 1024..65536)
+ *   stages         BULK, TMA: pipeline depth (2..8); shared memory = stages*tile_bytes*inputs
  *   fp64_mul       FP64 SCALE and TRIAD: where the product c*q is computed.  0 = the FP64
  *                  pipe; 1 = the integer units (an exact round-to-nearest-even binary64 multiply
  *                  that defers to the FP64 pipe for zero, subnormal, infinite and NaN operands
@@ -203,7 +210,9 @@ int sx_copy_d2h_async(void *host, const sx_array *src, size_t n);
 /* ---- executors: Section 3.3, Listing 2 and Section 4.2 (CUDA executor) ---------------- */
 typedef struct sx_executor sx_executor;
 /* `cfg` NULL (or variant AUTO) lets each call pick its launch shape (autotuner table first,
- * then the built-in default).  The executor keeps a copy of *cfg. */
+ * then the built-in default).  The executor keeps a copy of *cfg, checked here as for a
+ * one-input call (SX_ERR_INVALID); a BULK or TMA shape whose shared memory fits one input array
+ * but not two is refused by each two-input call (add, triad) with SX_ERR_INVALID. */
 int sx_executor_create(sx_target *t, sx_policy policy, const sx_launch_cfg *cfg, sx_executor **out);
 /* Free the executor and the CUDA graphs it keeps (work it enqueued is not waited for). */
 int sx_executor_destroy(sx_executor *e);
@@ -351,8 +360,8 @@ int sx_batch_destroy(sx_batch *b);
 int sx_batch_run_noalloc(void *stream, const sx_batch_item *items, size_t count, const sx_batch_cfg *cfg);
 
 /* ---- autotuner ------------------------------------------------------------------------ */
-/* Time the candidate launch shapes (both variants, vector widths, unroll, block counts,
- * cache hints, bulk tile sizes) for (op, dtype, n) on scratch arrays the tuner allocates on the
+/* Time the candidate launch shapes (the three families, vector widths, unroll, block counts,
+ * cache hints, bulk tile sizes and pipeline depths) for (op, dtype, n) on scratch arrays the tuner allocates on the
  * target, keep the fastest in the in-process table (keyed by device name, op, dtype and
  * log2(n) bucket) and return it.  *gbs = its bandwidth (STREAM byte count). */
 int sx_tune(sx_target *t, sx_op op, sx_dtype dtype, size_t n, sx_launch_cfg *best, float *gbs);
@@ -387,7 +396,7 @@ typedef struct sx_server_cfg {
                                 at a time, so the rest stays open to smaller ones             */
     int32_t mode;            /* SX_SERVE_CONTINUOUS or SX_SERVE_FIFO                          */
     int32_t max_active;      /* requests admitted at once (slots), 1..65536; 0 = 256          */
-    int32_t chunk_bytes;     /* CONTINUOUS: byte budget of one step (1 MiB..2 GiB); 0 = 512 MiB */
+    int32_t chunk_bytes;     /* CONTINUOUS: byte budget of one step (1 MiB..2 GiB); 0 = 1 GiB   */
     int32_t steps_in_flight; /* CONTINUOUS: launched steps not yet completed (1..8); 0 = 2    */
     int32_t threads, blocks_per_sm, vec_bytes;  /* batched-kernel shape; 0 = default        */
     int32_t tile_bytes;      /* CONTINUOUS: work-tile bytes of the batched kernel; 0 = 256 KiB */

@@ -18,6 +18,17 @@
 // role leaves its loop; after the block's final barrier thread 0 waits (again bounded) for the
 // loads still in flight before shared memory is released.  Nothing traps.
 //
+// TMA family (k_stream_tma): the same pipeline with the results written back by bulk stores as
+// well, and a third role.  Consumers (warps 2..) compute each tile in place in its input slot
+// (x slot <- op(x, y)), make their shared-memory writes visible to the async proxy
+// (fence.proxy.async) and arrive on the slot's `done` mbarrier (one arrival per warp).  The
+// storer, lane 0 of warp 1, waits for `done`, issues one cp.async.bulk shared->global store of
+// the tile, and once the store of the tile before has finished reading its slot
+// (cp.async.bulk.wait_group.read 1) hands that slot back to the producer (`empty`, one arrival).
+// For copy there is nothing to compute: the storer takes each slot as soon as it is full, so a
+// tile crosses the SM without passing through a register.  Before the block exits the storer
+// waits until its stores are complete.
+
 // Alignment: every bulk copy starts on a 16-byte boundary and moves a multiple of 16 bytes.
 // Elements before the first 16-byte boundary and after the last whole 16 bytes are done one
 // by one.  Arrays whose addresses differ modulo 16 bytes take the VECTOR family instead.
@@ -98,6 +109,17 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t phase
         if (*abort || global_ns() - t0 > kWaitLimitNs) return false;
     }
 }
+
+__device__ __forceinline__ void bulk_store(void *dst, const void *src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src_smem)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the bulk stores of all but the most recent group have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_but_one() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// all bulk stores issued by this thread are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 template <int OP, class T, int MM>
 __global__ void __launch_bounds__(1024, 1)
@@ -225,6 +247,131 @@ k_stream_bulk(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_
     }
 }
 
+template <int OP, class T, int MM>
+__global__ void __launch_bounds__(1024, 1)
+k_stream_tma(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t nbody,
+             uint32_t tile_elems, int stages, T q, int *err) {
+    constexpr bool HAS_Y = (OP == SX_OP_ADD || OP == SX_OP_TRIAD);
+    constexpr bool COMPUTE = OP != SX_OP_COPY;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kMaxStages];
+    __shared__ __align__(8) uint64_t done[kMaxStages];
+    __shared__ __align__(8) uint64_t empty[kMaxStages];
+    __shared__ int abort_flag;
+
+    // scalar edges: [0, head) and [head + nbody, n)
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t body_end = head + nbody;
+    if (gtid < head + (n - body_end)) {
+        const uint64_t i = gtid < head ? gtid : body_end + (gtid - head);
+        const T yv = HAS_Y ? y[i] : T(0);
+        out[i] = apply_op<OP, T>(x[i], yv, q);
+    }
+
+    const uint64_t ntiles = (nbody + tile_elems - 1) / tile_elems;
+    const uint64_t nlocal = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    if (nlocal == 0) return;  // uniform across the block
+
+    const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(T);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t consumer_warps = COMPUTE ? blockDim.x / 32 - 2 : 0;
+    const T *xb = x + head;
+    const T *yb = HAS_Y ? y + head : nullptr;
+    T *ob = out + head;
+    auto slot_x = [&](int s) { return smem + (size_t)s * (HAS_Y ? 2u : 1u) * tile_bytes; };
+    auto slot_y = [&](int s) { return smem + (size_t)s * 2u * tile_bytes + tile_bytes; };
+    auto tile_start = [&](uint64_t j) { return (blockIdx.x + j * gridDim.x) * (uint64_t)tile_elems; };
+    auto tile_len = [&](uint64_t j) { return (uint32_t)(min((uint64_t)tile_elems, nbody - tile_start(j)) * sizeof(T)); };
+    auto phase = [&](uint64_t j) { return (uint32_t)((j / (uint64_t)stages) & 1); };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            if (COMPUTE) mbar_init(&done[s], consumer_warps);
+            mbar_init(&empty[s], 1);  // the storing thread hands each slot back
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_async_smem();
+    }
+    __syncthreads();
+    volatile int *abort_v = &abort_flag;
+
+    uint64_t issued = 0;  // producer only: tiles whose loads were issued
+    if (warp == 0) {
+        if (lane == 0) {
+            for (uint64_t j = 0; j < nlocal; ++j) {
+                const int s = (int)(j % (uint64_t)stages);
+                if (j >= (uint64_t)stages && !mbar_wait_or_abort(&empty[s], phase(j) ^ 1u, abort_v)) {
+                    *abort_v = 1;
+                    break;
+                }
+                const uint32_t bytes = tile_len(j);
+                mbar_expect_tx(&full[s], HAS_Y ? 2 * bytes : bytes);
+                bulk_load(slot_x(s), xb + tile_start(j), bytes, &full[s]);
+                if constexpr (HAS_Y) bulk_load(slot_y(s), yb + tile_start(j), bytes, &full[s]);
+                issued = j + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // storer: a tile leaves once it is computed (copy: once it has arrived); its slot goes
+            // back to the producer when the store of the next tile has been issued and this one's
+            // has finished reading shared memory
+            for (uint64_t j = 0; j < nlocal; ++j) {
+                const int s = (int)(j % (uint64_t)stages);
+                if (!mbar_wait_or_abort(COMPUTE ? &done[s] : &full[s], phase(j), abort_v)) {
+                    *abort_v = 1;
+                    break;
+                }
+                bulk_store(ob + tile_start(j), slot_x(s), tile_len(j));
+                bulk_commit();
+                bulk_wait_read_but_one();
+                if (j >= 1) mbar_arrive(&empty[(int)((j - 1) % (uint64_t)stages)]);
+            }
+            bulk_wait_all();  // the stores are complete before the block exits
+        }
+    } else if (COMPUTE) {
+        const uint32_t ctid = threadIdx.x - 64, ncons = blockDim.x - 64;
+        for (uint64_t j = 0; j < nlocal; ++j) {
+            const int s = (int)(j % (uint64_t)stages);
+            // one decision per warp, as in k_stream_bulk
+            const bool ok = mbar_wait_or_abort(&full[s], phase(j), abort_v);
+            if (!__all_sync(0xffffffffu, ok)) {
+                *abort_v = 1;
+                break;
+            }
+            const uint32_t nv = tile_len(j) / 16;
+            const uint32_t sx0 = smem_addr(slot_x(s));
+            const uint32_t sy0 = HAS_Y ? smem_addr(slot_y(s)) : 0u;
+            for (uint32_t v = ctid; v < nv; v += ncons) {
+                uint64_t a0, a1, b0 = 0, b1 = 0;
+                asm volatile("ld.shared.v2.u64 {%0,%1}, [%2];" : "=l"(a0), "=l"(a1) : "r"(sx0 + 16 * v));
+                if constexpr (HAS_Y)
+                    asm volatile("ld.shared.v2.u64 {%0,%1}, [%2];" : "=l"(b0), "=l"(b1) : "r"(sy0 + 16 * v));
+                const uint64_t r0 = op_word<OP, T, MM>(a0, b0, q, 0);
+                const uint64_t r1 = op_word<OP, T, MM>(a1, b1, q, 1);
+                asm volatile("st.shared.v2.u64 [%0], {%1,%2};" ::"r"(sx0 + 16 * v), "l"(r0), "l"(r1) : "memory");
+            }
+            fence_async_smem();  // this thread's results are visible to the bulk store
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&done[s]);
+        }
+    }
+    __syncthreads();  // every role has left its loop (all waits above are bounded)
+    if (threadIdx.x == 0 && *abort_v) {
+        atomicExch(err, kErrBulkWait);
+        const uint64_t first = issued > (uint64_t)stages ? issued - (uint64_t)stages : 0;
+        for (uint64_t k = first; k < issued; ++k) {
+            const int s = (int)(k % (uint64_t)stages);
+            if (!mbar_wait_bounded(&full[s], phase(k), kWaitLimitNs)) {
+                atomicExch(err, kErrBulkDrain);
+                break;
+            }
+        }
+    }
+}
+
 // Per device and kernel instantiation: the dynamic shared memory limit already raised, and the
 // resident blocks per SM of each (threads, shared memory) shape.  Setting the attribute and
 // querying occupancy cost several microseconds of host time, more than a small launch runs.
@@ -276,13 +423,14 @@ int launch_bulk_t(const sx_target *t, cudaStream_t st, const T *x, const T *y, T
     const uint32_t tile_elems = (uint32_t)(c.tile_bytes / es);
     const size_t smem = (size_t)c.stages * (HAS_Y ? 2 : 1) * c.tile_bytes;
     constexpr bool MUL64 = sizeof(T) == 8 && (OP == SX_OP_SCALE || OP == SX_OP_TRIAD);
-    auto kern = k_stream_bulk<OP, T, 0>;
+    const bool tma = c.variant == SX_VARIANT_TMA;
+    auto kern = tma ? k_stream_tma<OP, T, 0> : k_stream_bulk<OP, T, 0>;
     if constexpr (MUL64) {
         switch (mul_variant(c.fp64_mul, (double)q)) {
-            case 1: kern = k_stream_bulk<OP, T, 1>; break;
-            case 2: kern = k_stream_bulk<OP, T, 2>; break;
-            case 3: kern = k_stream_bulk<OP, T, 3>; break;
-            case 4: kern = k_stream_bulk<OP, T, 4>; break;
+            case 1: kern = tma ? k_stream_tma<OP, T, 1> : k_stream_bulk<OP, T, 1>; break;
+            case 2: kern = tma ? k_stream_tma<OP, T, 2> : k_stream_bulk<OP, T, 2>; break;
+            case 3: kern = tma ? k_stream_tma<OP, T, 3> : k_stream_bulk<OP, T, 3>; break;
+            case 4: kern = tma ? k_stream_tma<OP, T, 4> : k_stream_bulk<OP, T, 4>; break;
             default: break;
         }
     }
@@ -318,8 +466,11 @@ int dispatch_bulk(const sx_target *t, cudaStream_t s, int op, const void *x, con
 
 int validate_bulk_cfg(const sx_target *t, int op, const sx_launch_cfg &c) {
     if (c.threads < 64 || c.threads > 1024 || c.threads % 32)
-        return fail(SX_ERR_INVALID, "BULK threads=%d: need a multiple of 32 in [64, 1024] (a producer warp "
+        return fail(SX_ERR_INVALID, "BULK/TMA threads=%d: need a multiple of 32 in [64, 1024] (a producer warp "
                     "and at least one consumer warp)", c.threads);
+    if (c.variant == SX_VARIANT_TMA && c.threads < 96)
+        return fail(SX_ERR_INVALID, "TMA threads=%d: need at least 96 (producer, storer and consumer warps)",
+                    c.threads);
     if (c.tile_bytes < 1024 || c.tile_bytes > 65536 || c.tile_bytes % 1024)
         return fail(SX_ERR_INVALID, "BULK tile_bytes=%d: need a multiple of 1024 in [1024, 65536]", c.tile_bytes);
     if (c.stages < 2 || c.stages > kMaxStages)

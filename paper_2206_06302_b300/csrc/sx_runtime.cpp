@@ -422,8 +422,10 @@ int sx_executor_create(sx_target *t, sx_policy policy, const sx_launch_cfg *cfg,
     if (cfg && cfg->variant != SX_VARIANT_AUTO) {
         e->fixed_cfg = true;
         e->cfg = *cfg;
-        const sx_launch_cfg full = resolve_cfg(t, SX_OP_TRIAD, SX_F64, 1, &e->cfg);
-        int s = validate_cfg(t, SX_OP_TRIAD, full);
+        // the shape is checked here as for a one-input call; calls with two inputs check again
+        // (BULK and TMA stage twice the shared memory for them)
+        const sx_launch_cfg full = resolve_cfg(t, SX_OP_SCALE, SX_F64, 1, &e->cfg);
+        int s = validate_cfg(t, SX_OP_SCALE, full);
         if (s != SX_OK) {
             delete e;
             return s;

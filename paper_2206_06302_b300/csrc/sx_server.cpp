@@ -598,7 +598,7 @@ int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out) {
     if (c.mode != SX_SERVE_CONTINUOUS && c.mode != SX_SERVE_FIFO) return fail(SX_ERR_INVALID, "mode %d", c.mode);
     if (c.budget_bytes == 0) return fail(SX_ERR_INVALID, "budget_bytes must be positive");
     if (c.max_active == 0) c.max_active = 256;
-    if (c.chunk_bytes == 0) c.chunk_bytes = 512 << 20;
+    if (c.chunk_bytes == 0) c.chunk_bytes = 1 << 30;
     if (c.steps_in_flight == 0) c.steps_in_flight = 2;
     if (c.policy != SX_SERVE_POLICY_SHORT_FIRST && c.policy != SX_SERVE_POLICY_FAIR &&
         c.policy != SX_SERVE_POLICY_SRPT)

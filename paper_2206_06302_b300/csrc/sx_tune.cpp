@@ -180,7 +180,7 @@ void tune_batch_store(const sx_target *t, double mean_item_bytes, const sx_batch
 
 // Candidate shapes: a first pass over the per-thread access pattern (vector width, unroll,
 // cache hint) at a fixed block shape, then a pass over the block shape (threads, blocks per
-// SM or one tile per block) for the best access pattern, then the BULK family.
+// SM or one tile per block) for the best access pattern, then the BULK and TMA families.
 static bool mul64(int op, int dtype) { return dtype == SX_F64 && (op == SX_OP_SCALE || op == SX_OP_TRIAD); }
 
 static std::vector<sx_launch_cfg> vector_pass1(int op, int dtype) {
@@ -225,6 +225,26 @@ static std::vector<sx_launch_cfg> bulk_candidates(int op, int dtype) {
                 for (int bps : {1, 2}) {
                     sx_launch_cfg c{};
                     c.variant = SX_VARIANT_BULK;
+                    c.threads = th;
+                    c.blocks_per_sm = bps;
+                    c.tile_bytes = tile;
+                    c.stages = st;
+                    c.fp64_mul = mm;
+                    v.push_back(c);
+                }
+    return v;
+}
+
+static std::vector<sx_launch_cfg> tma_candidates(int op, int dtype) {
+    std::vector<sx_launch_cfg> v;
+    const int mm = mul64(op, dtype) ? 2 : 0;
+    const std::vector<int> threads = op == SX_OP_COPY ? std::vector<int>{96} : std::vector<int>{128, 256, 512};
+    for (int tile : {8192, 16384, 32768})
+        for (int st : {3, 4})
+            for (int th : threads)
+                for (int bps : {1, 2, 4}) {
+                    sx_launch_cfg c{};
+                    c.variant = SX_VARIANT_TMA;
                     c.threads = th;
                     c.blocks_per_sm = bps;
                     c.tile_bytes = tile;
@@ -281,6 +301,7 @@ int sx_tune(sx_target *t, sx_op op, sx_dtype dtype, size_t n, sx_launch_cfg *bes
         const sx_launch_cfg b1 = best;
         for (const auto &c : vector_pass2(b1)) try_cfg(c);
         for (const auto &c : bulk_candidates(op, dtype)) try_cfg(c);
+        for (const auto &c : tma_candidates(op, dtype)) try_cfg(c);
         clear_error();
         if (best.variant == 0) st = fail(SX_ERR_CUDA, "no candidate launch shape ran");
         else st = check_device_error(t);

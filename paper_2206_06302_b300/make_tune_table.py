@@ -1,6 +1,6 @@
 """Builds the tuner table shipped with the package (``tune_b300.json``).
 
-Runs ``sx_tune`` (every candidate launch shape of both kernel families, timed on scratch
+Runs ``sx_tune`` (every candidate launch shape of the three kernel families, timed on scratch
 arrays) for the four STREAM kernels in binary64 and binary32 at array sizes 2^lo .. 2^hi, and
 writes the table with ``sx_tune_save``.  Entries the table already holds for this device are
 kept unless ``--retune``.  Run it on the GPU model the table is for:

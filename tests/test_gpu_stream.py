@@ -37,6 +37,13 @@ CFGS = [
     dict(variant=sx.SX_VARIANT_BULK, threads=512, blocks_per_sm=1, tile_bytes=16384, stages=6,
          fp64_mul=2),
     dict(variant=sx.SX_VARIANT_BULK, threads=256, blocks_per_sm=1, tile_bytes=32768, stages=3),
+    # TMA both ways (results computed in place in shared memory and written by bulk stores)
+    dict(variant=sx.SX_VARIANT_TMA, threads=96, blocks_per_sm=1, tile_bytes=1024, stages=2),
+    dict(variant=sx.SX_VARIANT_TMA, threads=128, blocks_per_sm=2, tile_bytes=4096, stages=3,
+         fp64_mul=1),
+    dict(variant=sx.SX_VARIANT_TMA, threads=512, blocks_per_sm=1, tile_bytes=16384, stages=6,
+         fp64_mul=2),
+    dict(variant=sx.SX_VARIANT_TMA, threads=256, blocks_per_sm=4, tile_bytes=8192, stages=4),
 ]
 
 
@@ -157,6 +164,28 @@ def test_argument_errors(target, executor):
         sx.sx_free(h)
 
 
+@pytest.mark.parametrize("variant", [sx.SX_VARIANT_BULK, sx.SX_VARIANT_TMA])
+def test_staging_shape_for_one_input_only(target, variant):
+    """A staging shape of 3 x 64 KiB fits shared memory for one input array but not for two: the
+    executor takes it, copy and scale run with it (oracle bits), add and triad refuse it."""
+    e = sx.sx_executor_create(target, sx.SX_PAR, dict(variant=variant, threads=256, blocks_per_sm=1,
+                                                      tile_bytes=65536, stages=3))
+    n = (1 << 20) + 3
+    x, y = _inputs(n, np.float64, salt=5)
+    dx, dy, do = to_device(target, x), to_device(target, y), empty(target, np.float64, n)
+    sx.sx_copy(e, dx, do)
+    assert_bitwise(to_host(do), oracle.copy(x), "copy")
+    sx.sx_transform_scale(e, dx, do, 3.0)
+    assert_bitwise(to_host(do), oracle.scale(x, 3.0), "scale")
+    for op in (sx.SX_OP_ADD, sx.SX_OP_TRIAD):
+        with pytest.raises(sx.SxError) as ei:
+            sx.sx_execute(e, op, dx, dy, do, 3.0)
+        assert ei.value.status == sx.SX_ERR_INVALID
+    for h in (dx, dy, do):
+        sx.sx_free(h)
+    sx.sx_executor_destroy(e)
+
+
 def test_budget_is_enforced_on_the_host():
     t = sx.sx_target_create_ext(0, None, 1 << 20)
     a = sx.sx_alloc(t, sx.SX_F64, 1000)
@@ -226,7 +255,7 @@ def test_stream_passes_match_oracle(target, executor, dt, fused):
 def test_stream_iter_graphs_match_oracle(target, cfg):
     """Passes replayed from captured CUDA graphs (37 = 16 + 16 + 5 passes, then the same call
     again from the executor's cache) give the oracle's bits for every launch shape, including the
-    TMA family, in both types."""
+    bulk-copy families, in both types."""
     e = sx.sx_executor_create(target, sx.SX_PAR, CFGS[cfg])
     try:
         for dt, n in ((np.float64, 65536 + 7), (np.float32, 4099)):
@@ -459,7 +488,7 @@ def _random_doubles(n, seed):
     return w.view(np.float64).copy()
 
 
-@pytest.mark.parametrize("variant", [sx.SX_VARIANT_VECTOR, sx.SX_VARIANT_BULK])
+@pytest.mark.parametrize("variant", [sx.SX_VARIANT_VECTOR, sx.SX_VARIANT_BULK, sx.SX_VARIANT_TMA])
 def test_integer_unit_product_is_bit_identical(target, executor, variant):
     """fp64_mul=1/2 (integer-unit RN-even product with FP64-pipe fallback) == fp64_mul=0 bit for
     bit on every bit pattern, and == the oracle wherever the result is not a generated NaN."""
@@ -467,7 +496,7 @@ def test_integer_unit_product_is_bit_identical(target, executor, variant):
     x = _random_doubles(n, 31)
     y = _random_doubles(n, 32)
     base = dict(variant=variant, threads=256)
-    if variant == sx.SX_VARIANT_BULK:
+    if variant in (sx.SX_VARIANT_BULK, sx.SX_VARIANT_TMA):
         base.update(tile_bytes=8192, stages=3, blocks_per_sm=1)
     else:
         base.update(vec_bytes=32, unroll=2)
