@@ -696,7 +696,7 @@ def cpu_oracle_threads_gbs(n: int, seconds: float):
 def run_sweep(args):
     """Size sweep (the paper's array-size figure): n = 2^lo..2^hi per array, FP64 and FP32, the
     four kernels, VECTOR vs BULK (TMA bulk-copy staging of the inputs) vs TMA (bulk copies both
-    ways) at fixed launch shapes.  Prints one
+    ways) vs TMA_TENSOR (the same with 2-D tensor-map copies) at fixed launch shapes.  Prints one
     JSON line.  Back-to-back launches on the same arrays: below ~2^22-2^23 elements the three
     arrays stay in the 126 MB L2."""
     import torch
@@ -710,6 +710,8 @@ def run_sweep(args):
                      stages=3, fp64_mul=2),
         "tma": dict(variant=sx.SX_VARIANT_TMA, threads=256, blocks_per_sm=2, tile_bytes=16384,
                     stages=3, fp64_mul=2),
+        "tma_tensor": dict(variant=sx.SX_VARIANT_TMA_TENSOR, threads=256, blocks_per_sm=2,
+                           tile_bytes=16384, stages=3, fp64_mul=2),
     }
     execs = {k: sx.sx_executor_create(t, sx.SX_PAR_TASK, v) for k, v in shapes.items()}
     ops = (("copy", sx.SX_OP_COPY, 2), ("scale", sx.SX_OP_SCALE, 2), ("add", sx.SX_OP_ADD, 3),
@@ -780,8 +782,12 @@ def run_ours(args):
                     sx.sx_tune(t, op, dcode, tune_n)
         if args.tune_cache:
             sx.sx_tune_save(args.tune_cache)
-    forced = {"vector": dict(variant=sx.SX_VARIANT_VECTOR), "bulk": dict(variant=sx.SX_VARIANT_BULK),
-              "tma": dict(variant=sx.SX_VARIANT_TMA)}
+    # a forced family takes its default shape, with half of the FP64 products on the integer units
+    # as the tuned shapes have them (ignored for FP32 and for copy and add)
+    forced = {"vector": dict(variant=sx.SX_VARIANT_VECTOR, fp64_mul=2),
+              "bulk": dict(variant=sx.SX_VARIANT_BULK, fp64_mul=2),
+              "tma": dict(variant=sx.SX_VARIANT_TMA, fp64_mul=2),
+              "tma_tensor": dict(variant=sx.SX_VARIANT_TMA_TENSOR, fp64_mul=2)}
     e_auto = sx.sx_executor_create(t, sx.SX_PAR_TASK, forced.get(args.variant))
     execs = {}  # per dtype and op: an executor fixed to the shape resolved at tune_n
     for dcode, dname in ((sx.SX_F64, "f64"), (sx.SX_F32, "f32")):
@@ -979,7 +985,7 @@ def main(argv=None):
                     help="seeded uniform [-1,1) inputs, or a=1, b=2, c=0")
     ap.add_argument("--stream-doubling", action="store_true",
                     help="double a once after construction, as classic STREAM does before timing")
-    ap.add_argument("--variant", choices=["auto", "vector", "bulk", "tma"], default="auto",
+    ap.add_argument("--variant", choices=["auto", "vector", "bulk", "tma", "tma_tensor"], default="auto",
                     help="kernel family of the timed passes (auto: the tuner table)")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the step benchmark: the size sweep, vector vs the two TMA bulk-copy families")

@@ -86,23 +86,28 @@ typedef enum sx_policy { SX_PAR = 1, SX_PAR_TASK = 2 } sx_policy;
  * TMA: the BULK pipeline with the results written back by bulk copies as well: consumer warps
  * compute each tile in place in shared memory and a storer warp issues one cp.async.bulk
  * shared->global per tile (copy: the storer takes each tile as it arrives, no consumer work).
+ * TMA_TENSOR: TMA with 2-D tensor-map copies (cp.async.bulk.tensor.2d; tensor maps encoded per
+ * call): each array's body is a view of rows of 256 elements, a tile is a box of whole rows
+ * (tile_bytes a multiple of 2048), elements after the last whole row are done one by one.
  * AUTO: the autotuner's choice for (op, dtype, size) if it has one, else a fixed default. */
 typedef enum sx_variant {
-    SX_VARIANT_AUTO = 0, SX_VARIANT_VECTOR = 1, SX_VARIANT_BULK = 2, SX_VARIANT_TMA = 3
+    SX_VARIANT_AUTO = 0, SX_VARIANT_VECTOR = 1, SX_VARIANT_BULK = 2, SX_VARIANT_TMA = 3,
+    SX_VARIANT_TMA_TENSOR = 4
 } sx_variant;
 
 /* Launch configuration of one algorithm call.  A zero field means "default".
  *   threads        threads per block (multiple of 32; VECTOR: 32..1024; BULK: 64..1024, a producer
- *                  warp and consumer warps; TMA: 96..1024, a producer warp, a storer warp and
- *                  consumer warps, which copy leaves idle)
+ *                  warp and consumer warps; TMA, TMA_TENSOR: 96..1024, a producer warp, a storer
+ *                  warp and consumer warps, which copy leaves idle)
  *   blocks_per_sm  VECTOR: grid = SMs * blocks_per_sm with a grid-stride loop; 0 = one tile
- *                  per block (grid covers the array).  BULK, TMA: persistent blocks per SM (1..4)
+ *                  per block (grid covers the array).  BULK, TMA*: persistent blocks per SM (1..4)
  *   vec_bytes      VECTOR: 16 or 32 bytes per thread access
  *   unroll         VECTOR: vector accesses per thread per tile (1, 2 or 4)
  *   cache_hint     VECTOR: 0 = default caching, 1 = streaming (L1 no-allocate loads with an
  *                  L2 256-byte prefetch hint, evict-first stores)
- *   tile_bytes     BULK, TMA: bytes per array per pipeline stage (multiple of 1024, 1024..65536)
- *   stages         BULK, TMA: pipeline depth (2..8); shared memory = stages*tile_bytes*inputs
+ *   tile_bytes     BULK, TMA*: bytes per array per pipeline stage (multiple of 1024, 1024..65536;
+ *                  TMA_TENSOR: of 2048)
+ *   stages         BULK, TMA*: pipeline depth (2..8); shared memory = stages*tile_bytes*inputs
  *   fp64_mul       FP64 SCALE and TRIAD: where the product c*q is computed.  0 = the FP64
  *                  pipe; 1 = the integer units (an exact round-to-nearest-even binary64 multiply
  *                  that defers to the FP64 pipe for zero, subnormal, infinite and NaN operands

@@ -28,10 +28,21 @@
 // For copy there is nothing to compute: the storer takes each slot as soon as it is full, so a
 // tile crosses the SM without passing through a register.  Before the block exits the storer
 // waits until its stores are complete.
+//
+// TMA_TENSOR is the same kernel with 2-D tensor-map copies (cp.async.bulk.tensor.2d): each array's
+// body is described to the TMA unit as rows of 256 elements, a tile is a box of tile/256 rows, and
+// every copy starts at column 0 of its first row (so the 16-byte rule on the innermost coordinate
+// always holds).  The last tile may reach past the last row: the load fills those rows with zeros
+// and still completes the full box's byte count, the store writes only rows inside the array.
+// Elements after the last whole row are done one by one, like the unaligned head.
 
 // Alignment: every bulk copy starts on a 16-byte boundary and moves a multiple of 16 bytes.
 // Elements before the first 16-byte boundary and after the last whole 16 bytes are done one
 // by one.  Arrays whose addresses differ modulo 16 bytes take the VECTOR family instead.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -120,6 +131,29 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read_but_one() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 // all bulk stores issued by this thread are complete
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// The tensor maps of a TMA_TENSOR launch (kernel parameters; unused otherwise).
+struct TmaMaps {
+    CUtensorMap x, y, out;
+};
+
+// Box at (column c0, row c1) of `map` into shared memory, completing on `bar` (tx bytes).
+__device__ __forceinline__ void tensor_load_2d(void *dst_smem, const CUtensorMap *map, int32_t c0, int32_t c1,
+                                               uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Shared memory to the box at (column c0, row c1) of `map` (rows past the array are not written).
+__device__ __forceinline__ void tensor_store_2d(const CUtensorMap *map, int32_t c0, int32_t c1, const void *src_smem) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(smem_addr(src_smem))
+                 : "memory");
+}
 
 template <int OP, class T, int MM>
 __global__ void __launch_bounds__(1024, 1)
@@ -247,10 +281,12 @@ k_stream_bulk(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_
     }
 }
 
-template <int OP, class T, int MM>
+constexpr uint32_t kRowElems = 256;  // TMA_TENSOR: elements per row of the 2-D view
+
+template <int OP, class T, int MM, bool TENSOR>
 __global__ void __launch_bounds__(1024, 1)
 k_stream_tma(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t nbody,
-             uint32_t tile_elems, int stages, T q, int *err) {
+             uint32_t tile_elems, int stages, T q, int *err, const __grid_constant__ TmaMaps maps) {
     constexpr bool HAS_Y = (OP == SX_OP_ADD || OP == SX_OP_TRIAD);
     constexpr bool COMPUTE = OP != SX_OP_COPY;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -259,11 +295,11 @@ k_stream_tma(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t
     __shared__ __align__(8) uint64_t empty[kMaxStages];
     __shared__ int abort_flag;
 
-    // scalar edges: [0, head) and [head + nbody, n)
-    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // scalar edges: [0, head) and [head + nbody, n) (up to 255 elements after the last row)
     const uint64_t body_end = head + nbody;
-    if (gtid < head + (n - body_end)) {
-        const uint64_t i = gtid < head ? gtid : body_end + (gtid - head);
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < head + (n - body_end);
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = e < head ? e : body_end + (e - head);
         const T yv = HAS_Y ? y[i] : T(0);
         out[i] = apply_op<OP, T>(x[i], yv, q);
     }
@@ -275,6 +311,7 @@ k_stream_tma(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t
     const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(T);
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t consumer_warps = COMPUTE ? blockDim.x / 32 - 2 : 0;
+    auto tile_row = [&](uint64_t j) { return (int32_t)((blockIdx.x + j * gridDim.x) * (uint64_t)(tile_elems / kRowElems)); };
     const T *xb = x + head;
     const T *yb = HAS_Y ? y + head : nullptr;
     T *ob = out + head;
@@ -306,10 +343,17 @@ k_stream_tma(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t
                     *abort_v = 1;
                     break;
                 }
-                const uint32_t bytes = tile_len(j);
-                mbar_expect_tx(&full[s], HAS_Y ? 2 * bytes : bytes);
-                bulk_load(slot_x(s), xb + tile_start(j), bytes, &full[s]);
-                if constexpr (HAS_Y) bulk_load(slot_y(s), yb + tile_start(j), bytes, &full[s]);
+                if constexpr (TENSOR) {
+                    // a box always completes its full size, rows past the array filled with zeros
+                    mbar_expect_tx(&full[s], HAS_Y ? 2 * tile_bytes : tile_bytes);
+                    tensor_load_2d(slot_x(s), &maps.x, 0, tile_row(j), &full[s]);
+                    if constexpr (HAS_Y) tensor_load_2d(slot_y(s), &maps.y, 0, tile_row(j), &full[s]);
+                } else {
+                    const uint32_t bytes = tile_len(j);
+                    mbar_expect_tx(&full[s], HAS_Y ? 2 * bytes : bytes);
+                    bulk_load(slot_x(s), xb + tile_start(j), bytes, &full[s]);
+                    if constexpr (HAS_Y) bulk_load(slot_y(s), yb + tile_start(j), bytes, &full[s]);
+                }
                 issued = j + 1;
             }
         }
@@ -324,7 +368,8 @@ k_stream_tma(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t
                     *abort_v = 1;
                     break;
                 }
-                bulk_store(ob + tile_start(j), slot_x(s), tile_len(j));
+                if constexpr (TENSOR) tensor_store_2d(&maps.out, 0, tile_row(j), slot_x(s));
+                else bulk_store(ob + tile_start(j), slot_x(s), tile_len(j));
                 bulk_commit();
                 bulk_wait_read_but_one();
                 if (j >= 1) mbar_arrive(&empty[(int)((j - 1) % (uint64_t)stages)]);
@@ -399,10 +444,78 @@ int bulk_prepare(int device, const void *kern, int threads, size_t smem, int *oc
     return SX_OK;
 }
 
+// Kernel instantiation for the product unit `mv` (mul_variant; binary64 SCALE and TRIAD only).
+template <int OP, class T>
+auto bulk_kernel(int mv) {
+    constexpr bool MUL64 = sizeof(T) == 8 && (OP == SX_OP_SCALE || OP == SX_OP_TRIAD);
+    auto k = k_stream_bulk<OP, T, 0>;
+    if constexpr (MUL64) {
+        switch (mv) {
+            case 1: k = k_stream_bulk<OP, T, 1>; break;
+            case 2: k = k_stream_bulk<OP, T, 2>; break;
+            case 3: k = k_stream_bulk<OP, T, 3>; break;
+            case 4: k = k_stream_bulk<OP, T, 4>; break;
+            default: break;
+        }
+    }
+    return k;
+}
+
+template <int OP, class T, bool TENSOR>
+auto tma_kernel(int mv) {
+    constexpr bool MUL64 = sizeof(T) == 8 && (OP == SX_OP_SCALE || OP == SX_OP_TRIAD);
+    auto k = k_stream_tma<OP, T, 0, TENSOR>;
+    if constexpr (MUL64) {
+        switch (mv) {
+            case 1: k = k_stream_tma<OP, T, 1, TENSOR>; break;
+            case 2: k = k_stream_tma<OP, T, 2, TENSOR>; break;
+            case 3: k = k_stream_tma<OP, T, 3, TENSOR>; break;
+            case 4: k = k_stream_tma<OP, T, 4, TENSOR>; break;
+            default: break;
+        }
+    }
+    return k;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (the library does
+// not link the driver library itself).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// The 2-D view of `nrows` rows of kRowElems elements from `base` (16-byte aligned), in boxes of
+// `box_rows` rows; loads past the last row read zeros.
+int encode_row_map(CUtensorMap *m, const void *base, size_t es, uint64_t nrows, uint32_t box_rows) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(SX_ERR_STATE, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[2] = {kRowElems, nrows};
+    const cuuint64_t strides[1] = {kRowElems * es};
+    const cuuint32_t box[2] = {kRowElems, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                           const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SX_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    return SX_OK;
+}
+
 template <int OP, class T>
 int launch_bulk_t(const sx_target *t, cudaStream_t st, const T *x, const T *y, T *out, size_t n, T q,
                   const sx_launch_cfg &c) {
     constexpr bool HAS_Y = (OP == SX_OP_ADD || OP == SX_OP_TRIAD);
+    constexpr bool MUL64 = sizeof(T) == 8 && (OP == SX_OP_SCALE || OP == SX_OP_TRIAD);
     const uintptr_t mis = (uintptr_t)out % 16;
     const bool same = ((uintptr_t)x % 16 == mis) && (!HAS_Y || (uintptr_t)y % 16 == mis);
     const bool alias = (x == out) || (HAS_Y && y == out);
@@ -419,30 +532,44 @@ int launch_bulk_t(const sx_target *t, cudaStream_t st, const T *x, const T *y, T
     const size_t es = sizeof(T);
     size_t head = ((16 - mis) % 16) / es;
     if (head > n) head = n;
-    const uint64_t nbody = ((n - head) * es / 16) * 16 / es;
+    const bool tensor = c.variant == SX_VARIANT_TMA_TENSOR;
+    // the body: whole 16-byte units, or whole rows of the 2-D view
+    const uint64_t nrows = (n - head) / kRowElems;
+    const uint64_t nbody = tensor ? nrows * kRowElems : ((n - head) * es / 16) * 16 / es;
+    if (tensor && nrows >= (1ull << 31)) return fail(SX_ERR_INVALID, "array too long for the 2-D tensor view");
     const uint32_t tile_elems = (uint32_t)(c.tile_bytes / es);
     const size_t smem = (size_t)c.stages * (HAS_Y ? 2 : 1) * c.tile_bytes;
-    constexpr bool MUL64 = sizeof(T) == 8 && (OP == SX_OP_SCALE || OP == SX_OP_TRIAD);
-    const bool tma = c.variant == SX_VARIANT_TMA;
-    auto kern = tma ? k_stream_tma<OP, T, 0> : k_stream_bulk<OP, T, 0>;
-    if constexpr (MUL64) {
-        switch (mul_variant(c.fp64_mul, (double)q)) {
-            case 1: kern = tma ? k_stream_tma<OP, T, 1> : k_stream_bulk<OP, T, 1>; break;
-            case 2: kern = tma ? k_stream_tma<OP, T, 2> : k_stream_bulk<OP, T, 2>; break;
-            case 3: kern = tma ? k_stream_tma<OP, T, 3> : k_stream_bulk<OP, T, 3>; break;
-            case 4: kern = tma ? k_stream_tma<OP, T, 4> : k_stream_bulk<OP, T, 4>; break;
-            default: break;
-        }
-    }
+    const int mv = MUL64 ? mul_variant(c.fp64_mul, (double)q) : 0;
+    const void *kfn = c.variant == SX_VARIANT_BULK ? (const void *)bulk_kernel<OP, T>(mv)
+                      : tensor                     ? (const void *)tma_kernel<OP, T, true>(mv)
+                                                   : (const void *)tma_kernel<OP, T, false>(mv);
     int occ = 0;
-    SX_TRY(bulk_prepare(t->device, (const void *)kern, c.threads, smem, &occ));
-    if (occ < 1) return fail(SX_ERR_INVALID, "BULK shape does not fit on an SM (%zu B shared)", smem);
+    SX_TRY(bulk_prepare(t->device, kfn, c.threads, smem, &occ));
+    if (occ < 1) return fail(SX_ERR_INVALID, "BULK/TMA shape does not fit on an SM (%zu B shared)", smem);
     const int bps = c.blocks_per_sm < occ ? c.blocks_per_sm : occ;
     const uint64_t ntiles = (nbody + tile_elems - 1) / tile_elems;
     uint64_t grid = (uint64_t)t->sm_count * bps;
     if (grid > ntiles) grid = ntiles;
     if (grid == 0) grid = 1;
-    kern<<<(unsigned)grid, c.threads, smem, st>>>(x, y, out, n, head, nbody, tile_elems, c.stages, q, t->d_err);
+    if (c.variant == SX_VARIANT_BULK) {
+        bulk_kernel<OP, T>(mv)<<<(unsigned)grid, c.threads, smem, st>>>(x, y, out, n, head, nbody, tile_elems,
+                                                                        c.stages, q, t->d_err);
+    } else {
+        TmaMaps maps;
+        std::memset(&maps, 0, sizeof maps);
+        if (tensor && nrows > 0) {
+            const uint32_t box_rows = tile_elems / kRowElems;
+            SX_TRY(encode_row_map(&maps.x, x + head, es, nrows, box_rows));
+            SX_TRY(encode_row_map(&maps.y, HAS_Y ? y + head : x + head, es, nrows, box_rows));
+            SX_TRY(encode_row_map(&maps.out, out + head, es, nrows, box_rows));
+        }
+        if (tensor)
+            tma_kernel<OP, T, true>(mv)<<<(unsigned)grid, c.threads, smem, st>>>(
+                x, y, out, n, head, nbody, tile_elems, c.stages, q, t->d_err, maps);
+        else
+            tma_kernel<OP, T, false>(mv)<<<(unsigned)grid, c.threads, smem, st>>>(
+                x, y, out, n, head, nbody, tile_elems, c.stages, q, t->d_err, maps);
+    }
     SX_CUDA(cudaGetLastError());
     return SX_OK;
 }
@@ -468,9 +595,13 @@ int validate_bulk_cfg(const sx_target *t, int op, const sx_launch_cfg &c) {
     if (c.threads < 64 || c.threads > 1024 || c.threads % 32)
         return fail(SX_ERR_INVALID, "BULK/TMA threads=%d: need a multiple of 32 in [64, 1024] (a producer warp "
                     "and at least one consumer warp)", c.threads);
-    if (c.variant == SX_VARIANT_TMA && c.threads < 96)
+    const bool tma = c.variant == SX_VARIANT_TMA || c.variant == SX_VARIANT_TMA_TENSOR;
+    if (tma && c.threads < 96)
         return fail(SX_ERR_INVALID, "TMA threads=%d: need at least 96 (producer, storer and consumer warps)",
                     c.threads);
+    if (c.variant == SX_VARIANT_TMA_TENSOR && c.tile_bytes % 2048)
+        return fail(SX_ERR_INVALID, "TMA_TENSOR tile_bytes=%d: need whole rows of 256 binary64 elements "
+                    "(a multiple of 2048)", c.tile_bytes);
     if (c.tile_bytes < 1024 || c.tile_bytes > 65536 || c.tile_bytes % 1024)
         return fail(SX_ERR_INVALID, "BULK tile_bytes=%d: need a multiple of 1024 in [1024, 65536]", c.tile_bytes);
     if (c.stages < 2 || c.stages > kMaxStages)

@@ -355,10 +355,16 @@ sx_launch_cfg resolve_cfg(const sx_target *t, int op, int dtype, size_t n, const
         if (c.threads == 0) c.threads = 256;
         if (c.vec_bytes == 0) c.vec_bytes = 32;
         if (c.unroll == 0) c.unroll = 2;
-    } else if (c.variant == SX_VARIANT_BULK || c.variant == SX_VARIANT_TMA) {
-        if (c.threads == 0) c.threads = c.variant == SX_VARIANT_TMA && op == SX_OP_COPY ? 96 : 256;
+    } else if (c.variant == SX_VARIANT_BULK) {
+        if (c.threads == 0) c.threads = 256;
         if (c.blocks_per_sm == 0) c.blocks_per_sm = 1;
         if (c.tile_bytes == 0) c.tile_bytes = 16384;
+        if (c.stages == 0) c.stages = 4;
+    } else if (c.variant == SX_VARIANT_TMA || c.variant == SX_VARIANT_TMA_TENSOR) {
+        // the shape that did best over the four kernels at 2^27 (blocks per SM capped by shared memory)
+        if (c.threads == 0) c.threads = op == SX_OP_COPY ? 96 : 256;
+        if (c.blocks_per_sm == 0) c.blocks_per_sm = 4;
+        if (c.tile_bytes == 0) c.tile_bytes = 8192;
         if (c.stages == 0) c.stages = 4;
     }
     return c;
@@ -380,14 +386,15 @@ int validate_cfg(const sx_target *t, int op, const sx_launch_cfg &c) {
             return fail(SX_ERR_INVALID, "fp64_mul=%d: need 0, 1 or 2", c.fp64_mul);
         return SX_OK;
     }
-    if (c.variant == SX_VARIANT_BULK || c.variant == SX_VARIANT_TMA) return validate_bulk_cfg(t, op, c);
-    return fail(SX_ERR_INVALID, "variant=%d: need VECTOR (1), BULK (2) or TMA (3)", c.variant);
+    if (c.variant == SX_VARIANT_BULK || c.variant == SX_VARIANT_TMA || c.variant == SX_VARIANT_TMA_TENSOR)
+        return validate_bulk_cfg(t, op, c);
+    return fail(SX_ERR_INVALID, "variant=%d: need VECTOR (1), BULK (2), TMA (3) or TMA_TENSOR (4)", c.variant);
 }
 
 int launch_stream_op(const sx_target *t, cudaStream_t s, int op, int dtype, const void *x, const void *y,
                      void *out, size_t n, double q, const sx_launch_cfg &c) {
     if (n == 0) return SX_OK;
-    if (c.variant == SX_VARIANT_BULK || c.variant == SX_VARIANT_TMA)
+    if (c.variant == SX_VARIANT_BULK || c.variant == SX_VARIANT_TMA || c.variant == SX_VARIANT_TMA_TENSOR)
         return launch_bulk_op(t, s, op, dtype, x, y, out, n, q, c);
     if (dtype == SX_F64) return dispatch_op<double>(t, s, op, x, y, out, n, q, c);
     if (dtype == SX_F32) return dispatch_op<float>(t, s, op, x, y, out, n, q, c);

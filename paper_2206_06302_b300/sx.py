@@ -24,7 +24,7 @@ SX_ERR_TIMEOUT, SX_ERR_CUDA, SX_ERR_NOT_READY, SX_ERR_DEVICE, SX_ERR_STATE = 5, 
 SX_F32, SX_F64, SX_U8 = 1, 2, 3
 SX_OP_COPY, SX_OP_SCALE, SX_OP_ADD, SX_OP_TRIAD, SX_OP_SEED = 0, 1, 2, 3, 4
 SX_PAR, SX_PAR_TASK = 1, 2
-SX_VARIANT_AUTO, SX_VARIANT_VECTOR, SX_VARIANT_BULK, SX_VARIANT_TMA = 0, 1, 2, 3
+SX_VARIANT_AUTO, SX_VARIANT_VECTOR, SX_VARIANT_BULK, SX_VARIANT_TMA, SX_VARIANT_TMA_TENSOR = 0, 1, 2, 3, 4
 SX_FN_TO_UPPER, SX_FN_TO_LOWER = 1, 2
 SX_SERVE_CONTINUOUS, SX_SERVE_FIFO = 0, 1
 SX_SERVE_POLICY_SRPT, SX_SERVE_POLICY_FAIR, SX_SERVE_POLICY_SHORT_FIRST = 0, 1, 2

@@ -44,6 +44,12 @@ CFGS = [
     dict(variant=sx.SX_VARIANT_TMA, threads=512, blocks_per_sm=1, tile_bytes=16384, stages=6,
          fp64_mul=2),
     dict(variant=sx.SX_VARIANT_TMA, threads=256, blocks_per_sm=4, tile_bytes=8192, stages=4),
+    # the same with 2-D tensor-map copies (rows of 256 elements; boxes of 1..16 rows)
+    dict(variant=sx.SX_VARIANT_TMA_TENSOR, threads=96, blocks_per_sm=1, tile_bytes=2048, stages=2),
+    dict(variant=sx.SX_VARIANT_TMA_TENSOR, threads=128, blocks_per_sm=2, tile_bytes=4096, stages=3,
+         fp64_mul=1),
+    dict(variant=sx.SX_VARIANT_TMA_TENSOR, threads=256, blocks_per_sm=1, tile_bytes=16384, stages=4,
+         fp64_mul=2),
 ]
 
 
@@ -164,7 +170,7 @@ def test_argument_errors(target, executor):
         sx.sx_free(h)
 
 
-@pytest.mark.parametrize("variant", [sx.SX_VARIANT_BULK, sx.SX_VARIANT_TMA])
+@pytest.mark.parametrize("variant", [sx.SX_VARIANT_BULK, sx.SX_VARIANT_TMA, sx.SX_VARIANT_TMA_TENSOR])
 def test_staging_shape_for_one_input_only(target, variant):
     """A staging shape of 3 x 64 KiB fits shared memory for one input array but not for two: the
     executor takes it, copy and scale run with it (oracle bits), add and triad refuse it."""
@@ -183,6 +189,26 @@ def test_staging_shape_for_one_input_only(target, variant):
         assert ei.value.status == sx.SX_ERR_INVALID
     for h in (dx, dy, do):
         sx.sx_free(h)
+    sx.sx_executor_destroy(e)
+
+
+def test_tensor_map_tiles_are_whole_rows(target):
+    """TMA_TENSOR tiles are boxes of whole 256-element rows: a tile of 3 KiB is refused, and an
+    array shorter than one row (all of it done element by element) gives the oracle's bits."""
+    with pytest.raises(sx.SxError) as ei:
+        sx.sx_executor_create(target, sx.SX_PAR, dict(variant=sx.SX_VARIANT_TMA_TENSOR, threads=128,
+                                                      blocks_per_sm=1, tile_bytes=3072, stages=2))
+    assert ei.value.status == sx.SX_ERR_INVALID
+    e = sx.sx_executor_create(target, sx.SX_PAR, dict(variant=sx.SX_VARIANT_TMA_TENSOR, threads=128,
+                                                      blocks_per_sm=1, tile_bytes=2048, stages=2))
+    for n in (255, 256, 511, 513):
+        x, y = _inputs(n, np.float64, salt=n)
+        dx, dy, do = to_device(target, x), to_device(target, y), empty(target, np.float64, n)
+        sx.sx_transform_triad(e, dx, dy, do, 3.0)
+        assert_bitwise(to_host(do), oracle.triad(x, y, 3.0), f"n={n}")
+        assert sx.sx_array_guard_ok(do)
+        for h in (dx, dy, do):
+            sx.sx_free(h)
     sx.sx_executor_destroy(e)
 
 
@@ -488,7 +514,8 @@ def _random_doubles(n, seed):
     return w.view(np.float64).copy()
 
 
-@pytest.mark.parametrize("variant", [sx.SX_VARIANT_VECTOR, sx.SX_VARIANT_BULK, sx.SX_VARIANT_TMA])
+@pytest.mark.parametrize("variant", [sx.SX_VARIANT_VECTOR, sx.SX_VARIANT_BULK, sx.SX_VARIANT_TMA,
+                                     sx.SX_VARIANT_TMA_TENSOR])
 def test_integer_unit_product_is_bit_identical(target, executor, variant):
     """fp64_mul=1/2 (integer-unit RN-even product with FP64-pipe fallback) == fp64_mul=0 bit for
     bit on every bit pattern, and == the oracle wherever the result is not a generated NaN."""
@@ -496,7 +523,7 @@ def test_integer_unit_product_is_bit_identical(target, executor, variant):
     x = _random_doubles(n, 31)
     y = _random_doubles(n, 32)
     base = dict(variant=variant, threads=256)
-    if variant in (sx.SX_VARIANT_BULK, sx.SX_VARIANT_TMA):
+    if variant in (sx.SX_VARIANT_BULK, sx.SX_VARIANT_TMA, sx.SX_VARIANT_TMA_TENSOR):
         base.update(tile_bytes=8192, stages=3, blocks_per_sm=1)
     else:
         base.update(vec_bytes=32, unroll=2)
