@@ -1,6 +1,7 @@
-// sx_tune.cpp -- the launch-shape autotuner and its table.
+// sx_tune.cpp -- the launch-shape autotuner and its table, and the resolution of a call's launch
+// shape (the tuner's table or the caller's shape, with defaults filled in, then checked).
 //
-// For one (op, dtype, n) the tuner times candidate launch shapes of both kernel families on
+// For one (op, dtype, n) the tuner times candidate launch shapes of the kernel families on
 // scratch arrays and keeps the fastest.  The table is keyed by (device name, op, dtype,
 // floor(log2 n)) so that one measurement covers a size octave; executors with an AUTO
 // configuration look it up on every call.  Batch shapes are keyed by (device name,
@@ -176,6 +177,55 @@ bool tune_batch_lookup(const sx_target *t, double mean_item_bytes, sx_batch_cfg 
 void tune_batch_store(const sx_target *t, double mean_item_bytes, const sx_batch_cfg &cfg) {
     std::lock_guard<std::mutex> g(g_mu);
     g_batch[BatchKey{t->name, log2_bucket(mean_item_bytes)}] = cfg;
+}
+
+// ---- launch shapes: the tuner's table or the caller's shape, defaults filled in, then checked ----
+sx_launch_cfg resolve_cfg(const sx_target *t, int op, int dtype, size_t n, const sx_launch_cfg *req) {
+    sx_launch_cfg c{};
+    if (req && req->variant != SX_VARIANT_AUTO) {
+        c = *req;
+    } else if (!tune_table_lookup(t, op, dtype, n, &c)) {
+        c = sx_launch_cfg{};
+        c.variant = SX_VARIANT_VECTOR;
+    }
+    if (c.variant == SX_VARIANT_VECTOR) {
+        if (c.threads == 0) c.threads = 256;
+        if (c.vec_bytes == 0) c.vec_bytes = 32;
+        if (c.unroll == 0) c.unroll = 2;
+    } else if (c.variant == SX_VARIANT_BULK) {
+        if (c.threads == 0) c.threads = 256;
+        if (c.blocks_per_sm == 0) c.blocks_per_sm = 1;
+        if (c.tile_bytes == 0) c.tile_bytes = 16384;
+        if (c.stages == 0) c.stages = 4;
+    } else if (c.variant == SX_VARIANT_TMA || c.variant == SX_VARIANT_TMA_TENSOR) {
+        // the shape that did best over the four kernels at 2^27 (blocks per SM capped by shared memory)
+        if (c.threads == 0) c.threads = op == SX_OP_COPY ? 96 : 256;
+        if (c.blocks_per_sm == 0) c.blocks_per_sm = 4;
+        if (c.tile_bytes == 0) c.tile_bytes = 8192;
+        if (c.stages == 0) c.stages = 4;
+    }
+    return c;
+}
+
+int validate_cfg(const sx_target *t, int op, const sx_launch_cfg &c) {
+    if (c.variant == SX_VARIANT_VECTOR) {
+        if (c.threads < 32 || c.threads > 1024 || c.threads % 32)
+            return fail(SX_ERR_INVALID, "threads=%d: need a multiple of 32 in [32, 1024]", c.threads);
+        if (c.vec_bytes != 16 && c.vec_bytes != 32)
+            return fail(SX_ERR_INVALID, "vec_bytes=%d: need 16 or 32", c.vec_bytes);
+        if (c.unroll != 1 && c.unroll != 2 && c.unroll != 4)
+            return fail(SX_ERR_INVALID, "unroll=%d: need 1, 2 or 4", c.unroll);
+        if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64)
+            return fail(SX_ERR_INVALID, "blocks_per_sm=%d out of [0, 64]", c.blocks_per_sm);
+        if (c.cache_hint < 0 || c.cache_hint > 1)
+            return fail(SX_ERR_INVALID, "cache_hint=%d: need 0 or 1", c.cache_hint);
+        if (c.fp64_mul < 0 || c.fp64_mul > 2)
+            return fail(SX_ERR_INVALID, "fp64_mul=%d: need 0, 1 or 2", c.fp64_mul);
+        return SX_OK;
+    }
+    if (c.variant == SX_VARIANT_BULK || c.variant == SX_VARIANT_TMA || c.variant == SX_VARIANT_TMA_TENSOR)
+        return validate_bulk_cfg(t, op, c);
+    return fail(SX_ERR_INVALID, "variant=%d: need VECTOR (1), BULK (2), TMA (3) or TMA_TENSOR (4)", c.variant);
 }
 
 // Candidate shapes: a first pass over the per-thread access pattern (vector width, unroll,
