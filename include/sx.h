@@ -361,7 +361,7 @@ int sx_batch_destroy(sx_batch *b);
  * turns on a lock. */
 #define SX_NOALLOC_MAX_ITEMS 4096
 #define SX_NOALLOC_MAX_TILES 65536
-#define SX_NOALLOC_SCRATCH_BYTES 884736 /* 4096 items x 88 B + 65536 tiles x 8 B */
+#define SX_NOALLOC_SCRATCH_BYTES 950272 /* 4096 items x 104 B + 65536 tiles x 8 B */
 int sx_batch_run_noalloc(void *stream, const sx_batch_item *items, size_t count, const sx_batch_cfg *cfg);
 
 /* ---- autotuner ------------------------------------------------------------------------ */
@@ -458,6 +458,10 @@ typedef struct sx_server_stats {
     double host_step_seconds;  /* CONTINUOUS: host time spent building and launching steps */
     double host_admit_seconds; /* host time spent in admission passes                      */
     uint64_t cancelled;        /* requests cancelled (sx_server_cancel)                     */
+    uint64_t fused;            /* CONTINUOUS: short requests run as one construct-then-operate
+                                  piece                                                     */
+    uint64_t early_done;       /* CONTINUOUS: of those, DONE from the piece's own completion
+                                  word, before the step holding it had completed            */
 } sx_server_stats;
 
 /* Start a server thread on the target (its stream carries every launch).  Thread-safe calls:

@@ -35,8 +35,11 @@ struct DevItem {
     uint64_t seed, index_base;
     uint32_t tile_elems, ntiles;
     uint32_t mulv;  // product variant of FP64 SCALE/TRIAD (0, 2 or 4; see mul_sel)
-    uint32_t pad;
+    uint32_t pad;   // serving steps: bit 0 dependent, bit 1 construct-then-operate, bits 8.. 1 + completion word
+    uint64_t seed2; // construct-then-operate: seed of y (seed: of x)
+    double q3;      // construct-then-operate: upper end of the inputs' range (q2: lower end; q: the op's scalar)
 };
+constexpr uint32_t kPadDependent = 1u, kPadConstructThenOp = 2u;
 
 // Batches split each FP64 product between the integer units and the FP64 pipe.
 inline uint32_t item_mul_variant(const sx_batch_item &it) {
@@ -49,8 +52,10 @@ struct DevTile {
     uint32_t index;  // tile index within the item
 };
 
+// coherent: the inputs were written earlier in the same kernel, so the body reads them with
+// coherent loads instead of the read-only path.
 template <int OP, class T, int VB, int MM>
-__device__ __forceinline__ void tile_vector(const DevItem &it, uint64_t start, uint64_t cnt) {
+__device__ __forceinline__ void tile_vector(const DevItem &it, uint64_t start, uint64_t cnt, bool coherent) {
     constexpr int W = VB / 8;
     constexpr int EPV = VB / (int)sizeof(T);
     constexpr bool HY = has_y<OP>();
@@ -86,12 +91,16 @@ __device__ __forceinline__ void tile_vector(const DevItem &it, uint64_t start, u
         uint64_t xa[W], ya[W], xc[W], yc[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) ya[k] = yc[k] = 0;
-        ldv<VB, 0>(xb + v * VB, xa);
-        if constexpr (HY) ldv<VB, 0>(yb + v * VB, ya);
+        auto load = [coherent](const char *a, uint64_t(&w)[W]) {
+            if (coherent) ldv<VB, 2>(a, w);
+            else ldv<VB, 0>(a, w);
+        };
+        load(xb + v * VB, xa);
+        if constexpr (HY) load(yb + v * VB, ya);
         const bool two = PER == 2 && v2 < nvec;
         if (two) {
-            ldv<VB, 0>(xb + v2 * VB, xc);
-            if constexpr (HY) ldv<VB, 0>(yb + v2 * VB, yc);
+            load(xb + v2 * VB, xc);
+            if constexpr (HY) load(yb + v2 * VB, yc);
         }
         uint64_t r[W];
 #pragma unroll
@@ -115,28 +124,28 @@ __device__ __forceinline__ void tile_seed(const DevItem &it, uint64_t start, uin
 }
 
 template <int VB>
-__device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint64_t cnt) {
+__device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint64_t cnt, bool coherent = false) {
     const bool f64 = it.dtype == SX_F64;
     switch (it.op) {
         case SX_OP_COPY:
-            if (f64) tile_vector<SX_OP_COPY, double, VB, 0>(it, start, cnt);
-            else tile_vector<SX_OP_COPY, float, VB, 0>(it, start, cnt);
+            if (f64) tile_vector<SX_OP_COPY, double, VB, 0>(it, start, cnt, coherent);
+            else tile_vector<SX_OP_COPY, float, VB, 0>(it, start, cnt, coherent);
             break;
         case SX_OP_SCALE:
-            if (!f64) tile_vector<SX_OP_SCALE, float, VB, 0>(it, start, cnt);
-            else if (it.mulv == 4) tile_vector<SX_OP_SCALE, double, VB, 4>(it, start, cnt);
-            else if (it.mulv == 2) tile_vector<SX_OP_SCALE, double, VB, 2>(it, start, cnt);
-            else tile_vector<SX_OP_SCALE, double, VB, 0>(it, start, cnt);
+            if (!f64) tile_vector<SX_OP_SCALE, float, VB, 0>(it, start, cnt, coherent);
+            else if (it.mulv == 4) tile_vector<SX_OP_SCALE, double, VB, 4>(it, start, cnt, coherent);
+            else if (it.mulv == 2) tile_vector<SX_OP_SCALE, double, VB, 2>(it, start, cnt, coherent);
+            else tile_vector<SX_OP_SCALE, double, VB, 0>(it, start, cnt, coherent);
             break;
         case SX_OP_ADD:
-            if (f64) tile_vector<SX_OP_ADD, double, VB, 0>(it, start, cnt);
-            else tile_vector<SX_OP_ADD, float, VB, 0>(it, start, cnt);
+            if (f64) tile_vector<SX_OP_ADD, double, VB, 0>(it, start, cnt, coherent);
+            else tile_vector<SX_OP_ADD, float, VB, 0>(it, start, cnt, coherent);
             break;
         case SX_OP_TRIAD:
-            if (!f64) tile_vector<SX_OP_TRIAD, float, VB, 0>(it, start, cnt);
-            else if (it.mulv == 4) tile_vector<SX_OP_TRIAD, double, VB, 4>(it, start, cnt);
-            else if (it.mulv == 2) tile_vector<SX_OP_TRIAD, double, VB, 2>(it, start, cnt);
-            else tile_vector<SX_OP_TRIAD, double, VB, 0>(it, start, cnt);
+            if (!f64) tile_vector<SX_OP_TRIAD, float, VB, 0>(it, start, cnt, coherent);
+            else if (it.mulv == 4) tile_vector<SX_OP_TRIAD, double, VB, 4>(it, start, cnt, coherent);
+            else if (it.mulv == 2) tile_vector<SX_OP_TRIAD, double, VB, 2>(it, start, cnt, coherent);
+            else tile_vector<SX_OP_TRIAD, double, VB, 0>(it, start, cnt, coherent);
             break;
         case SX_OP_SEED:
             if (f64 && it.q == -1.0 && it.q2 == 1.0) tile_seed<double, true>(it, start, cnt);
@@ -145,6 +154,37 @@ __device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint
             break;
         default: break;
     }
+}
+
+// Construct-then-operate piece of a serving step (a whole short request): each tile's block
+// constructs the tile's x (and y) from their seeds exactly as a SEED item does, waits for its own
+// stores, then applies the operation to them, read back from memory with coherent loads.
+template <class T, bool PM1>
+__device__ __forceinline__ void tile_construct(const DevItem &it, void *arr, uint64_t seed, uint64_t start,
+                                               uint64_t cnt) {
+    const T lo = (T)it.q2;
+    const T span = (T)it.q3 - lo;  // RN(hi - lo) in T, as the host-side generator defines it
+    seed_range<T, PM1>(static_cast<T *>(arr) + start, cnt, seed, it.index_base + start, lo, span, threadIdx.x,
+                       blockDim.x);
+}
+
+// The construction half: the tile's x (and y); the block's threads then meet so that every
+// input is in memory before the operation half (run_tile with coherent loads) reads it.
+__device__ __forceinline__ void construct_tile_inputs(const DevItem &it, uint64_t start, uint64_t cnt) {
+    const bool f64 = it.dtype == SX_F64;
+    const bool hy = it.op == SX_OP_ADD || it.op == SX_OP_TRIAD;
+    void *x = const_cast<void *>(it.x), *y = const_cast<void *>(it.y);
+    if (f64 && it.q2 == -1.0 && it.q3 == 1.0) {
+        tile_construct<double, true>(it, x, it.seed, start, cnt);
+        if (hy) tile_construct<double, true>(it, y, it.seed2, start, cnt);
+    } else if (f64) {
+        tile_construct<double, false>(it, x, it.seed, start, cnt);
+        if (hy) tile_construct<double, false>(it, y, it.seed2, start, cnt);
+    } else {
+        tile_construct<float, false>(it, x, it.seed, start, cnt);
+        if (hy) tile_construct<float, false>(it, y, it.seed2, start, cnt);
+    }
+    __syncthreads();  // the tile's inputs are in memory before any thread reads them
 }
 
 template <int VB>
@@ -325,6 +365,8 @@ uint64_t fill_item(const sx_batch_item &it, int tile_bytes, DevItem &d) {
     d.index_base = it.index_base;
     d.mulv = item_mul_variant(it);
     d.pad = 0;
+    d.seed2 = 0;
+    d.q3 = 0.0;
     const uint64_t te = tile_elems_for(it, tile_bytes);
     d.tile_elems = (uint32_t)te;
     const uint64_t nt = (it.n + te - 1) / te;
@@ -432,6 +474,11 @@ struct StepParams {
     uint64_t seq;
     unsigned long long *done;
     unsigned int *counter;
+    // per-piece completion words (pieces with pad bits 8..): the block that finishes a piece's
+    // last tile sets fin_host[w] (host-mapped) to 1; fin_count[w] counts its finished tiles and is
+    // left at zero for the word's next use
+    unsigned long long *fin_host;
+    unsigned int *fin_count;
     uint32_t prefix[kStepMaxItems + 1];
     DevItem items[kStepMaxItems];
 };
@@ -456,13 +503,28 @@ __global__ void __launch_bounds__(1024) k_batch_step(const __grid_constant__ Ste
             else hi = mid;
         }
         const DevItem &it = p.items[lo];
-        if ((it.pad & 1u) && !waited) {
+        if ((it.pad & kPadDependent) && !waited) {
             asm volatile("griddepcontrol.wait;" ::: "memory");
             waited = true;
         }
         const uint64_t start = (uint64_t)(t - p.prefix[lo]) * it.tile_elems;
         const uint64_t cnt = min((uint64_t)it.tile_elems, it.n - start);
-        run_tile<VB>(it, start, cnt);
+        const bool construct_first = (it.pad & kPadConstructThenOp) != 0;
+        if (construct_first) construct_tile_inputs(it, start, cnt);
+        run_tile<VB>(it, start, cnt, construct_first);
+        const uint32_t w = it.pad >> 8;
+        if (w) {
+            // the piece's last finished tile publishes it (as the step's last block does below)
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                if (atomicAdd(p.fin_count + (w - 1), 1u) == it.ntiles - 1) {
+                    p.fin_count[w - 1] = 0u;
+                    __threadfence_system();
+                    *(volatile unsigned long long *)(p.fin_host + (w - 1)) = 1ull;
+                }
+            }
+        }
     }
     if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
     if (p.done) {
@@ -498,8 +560,8 @@ int step_warm(cudaStream_t stream) {
     return SX_OK;
 }
 
-int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const sx_batch_item *items, size_t count,
-                const sx_batch_cfg &cfg, const uint8_t *dependent, bool overlap, const StepReport *report) {
+int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const StepItem *items, size_t count,
+                const sx_batch_cfg &cfg, bool overlap, const StepReport *report) {
     if (!report) SX_TRY(step_slot_reserve(s, 0, 0));  // the completion event
     static thread_local StepParams p;   // 23 KB: kept off the stack
     // the launch that carries the completion report: the last one that has work
@@ -507,19 +569,38 @@ int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const sx_b
     for (size_t first = 0; first < count; first += kStepMaxItems) {
         const size_t m = std::min<size_t>(kStepMaxItems, count - first);
         for (size_t i = 0; i < m; ++i)
-            if (items[first + i].n) last = first;
+            if (items[first + i].item.n) last = first;
     }
     bool reported = false;
     for (size_t first = 0; first < count; first += kStepMaxItems) {
         const size_t m = std::min<size_t>(kStepMaxItems, count - first);
         uint32_t tiles = 0;
         for (size_t i = 0; i < m; ++i) {
-            const uint64_t nti = fill_item(items[first + i], cfg.chunk_bytes, p.items[i]);
+            const StepItem &si = items[first + i];
+            DevItem &d = p.items[i];
+            uint64_t nti = fill_item(si.item, cfg.chunk_bytes, d);
+            if (si.flags & kStepConstructThenOp) {
+                // tiles sized by the bytes of both phases: inputs written, then every array of the op
+                const sx_batch_item &it = si.item;
+                const bool hy = it.op == SX_OP_ADD || it.op == SX_OP_TRIAD;
+                const size_t per = (size_t)((hy ? 2 : 1) + op_arrays(it.op)) * dtype_size(it.dtype);
+                const uint64_t te = std::max<uint64_t>(64, (uint64_t)cfg.chunk_bytes / per / 64 * 64);
+                d.tile_elems = (uint32_t)te;
+                nti = (it.n + te - 1) / te;
+                d.ntiles = (uint32_t)std::min<uint64_t>(nti, 0xffffffffull);
+                d.seed2 = si.seed2;
+                d.q3 = si.hi;
+            }
             if ((uint64_t)tiles + nti > 0xffffffffull) return fail(SX_ERR_INVALID, "step has too many tiles");
-            p.items[i].pad = (dependent && dependent[first + i]) ? 1u : 0u;
+            if (si.fin_word && (!report || !report->fin_host || si.fin_word >= (1u << 24)))
+                return fail(SX_ERR_INVALID, "piece completion word without report words");
+            d.pad = (si.flags & kStepDependent ? kPadDependent : 0u) |
+                    (si.flags & kStepConstructThenOp ? kPadConstructThenOp : 0u) | (si.fin_word << 8);
             p.prefix[i] = tiles;
             tiles += (uint32_t)nti;
         }
+        p.fin_host = report ? report->fin_host : nullptr;
+        p.fin_count = report ? report->fin_count : nullptr;
         p.prefix[m] = tiles;
         p.count = (uint32_t)m;
         p.total_tiles = tiles;

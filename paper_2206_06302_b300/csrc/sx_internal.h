@@ -205,21 +205,39 @@ int step_slot_reserve(StepSlot &s, size_t items, size_t tiles);
 void step_slot_free(StepSlot &s);
 // Number of work tiles `items` are cut into with tiles of `tile_bytes`.
 size_t step_tile_count(const sx_batch_item *items, size_t count, int tile_bytes);
+// One piece of a serving step: a batch item and how the step treats it.
+//   kStepDependent        waits for the previous step to complete before its first tile
+//   kStepConstructThenOp  a whole short request: each tile constructs its range of x (and y) from
+//                         item.seed (and seed2) over [item.q2, hi), then applies item.op (scalar
+//                         item.q) to it, reading the inputs back; item.index_base is the generator
+//                         index of element 0
+// fin_word: 1 + index of the completion word the piece reports to when its last tile is done (0:
+// none).
+struct StepItem {
+    sx_batch_item item{};
+    uint32_t flags = 0;
+    uint32_t fin_word = 0;
+    uint64_t seed2 = 0;
+    double hi = 0.0;
+};
+constexpr uint32_t kStepDependent = 1u, kStepConstructThenOp = 2u;
 // Launch the batched kernel over `items` (tiles of cfg.chunk_bytes, items passed in the launch's
 // parameters) on `stream` and record s.done after it.  With `overlap` the launch may start while
-// the previous step still runs (programmatic dependent launch); items with dependent[i] != 0 wait
-// for the previous step to complete first.
+// the previous step still runs (programmatic dependent launch).
 // With `report`, no event is recorded: the step's last block to finish writes report->seq to the
 // host-mapped word report->done (report->counter: a zeroed device counter owned by the caller's
-// slot).  The step must have work.
+// slot), and pieces with a fin_word set fin_host[fin_word - 1] (host-mapped, device address) to 1
+// when their last tile is done (fin_count: zeroed device counters, one per word).  The step must
+// have work.
 struct StepReport {
     uint64_t seq;
     unsigned long long *done;  // device address of a host-mapped word
     unsigned int *counter;
+    unsigned long long *fin_host = nullptr;
+    unsigned int *fin_count = nullptr;
 };
-int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const sx_batch_item *items,
-                size_t count, const sx_batch_cfg &cfg, const uint8_t *dependent, bool overlap,
-                const StepReport *report = nullptr);
+int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const StepItem *items, size_t count,
+                const sx_batch_cfg &cfg, bool overlap, const StepReport *report = nullptr);
 // Launch the step kernels once with no work on `stream` and wait: module loading and other
 // first-launch costs are paid here rather than by the first step of a latency-bound caller.
 int step_warm(cudaStream_t stream);

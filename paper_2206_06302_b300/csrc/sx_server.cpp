@@ -9,14 +9,18 @@
 //
 // CONTINUOUS mode batches requests continuously.  A step is one launch of the batched kernel
 // (sx_batch.cu) over a list of pieces, passed in the launch's parameters: for active requests a
-// range of their current phase (phase 0 constructs x and y, phase 1 runs the operation; a request
-// never has both phases in one step).  The step's byte budget goes by policy, shortest remaining
-// work first by default, so short requests finish in a step or two while long ones advance in
-// the rest.  Up to steps_in_flight steps are queued on the stream and consecutive steps overlap
-// through programmatic dependent launch; a piece that needs the inputs built in a step not yet
-// known complete waits for it on the device.  The thread builds the next step while the GPU runs
-// the previous ones, admits arrivals between steps, and marks a request DONE when the step
-// holding its last piece has completed.
+// range of their current phase (phase 0 constructs x and y, phase 1 runs the operation).  The
+// step's byte budget goes by policy, shortest remaining work first by default, so short requests
+// finish in the first step that takes them while long ones advance in the rest.  Up to
+// steps_in_flight steps are queued on the stream and consecutive steps overlap through
+// programmatic dependent launch; a piece that needs the inputs built in a step not yet known
+// complete waits for it on the device.  The thread builds the next step while the GPU runs the
+// previous ones, admits arrivals between steps, and marks a request DONE when the step holding
+// its last piece has completed.  A short request (its whole work at most a quarter of a step's
+// budget) that a step takes whole runs as one construct-then-operate piece (each tile builds its
+// range of the inputs, then applies the operation to it) and reports its own completion: the
+// block that finishes its last tile sets a host-mapped word, and the request is DONE as soon as
+// the thread sees it, without waiting for the rest of the step.
 //
 // FIFO mode is the per-call baseline: each admitted request is enqueued at once as its own
 // launches (construct x, construct y, operation) in arrival order, like a client calling the
@@ -68,6 +72,8 @@ struct Request {
     uint64_t last_step = 0;   // CONTINUOUS: the last step that holds a piece of this request
     int readers = 0;          // sx_server_read copies in progress from the request's arrays
     bool free_deferred = false;  // released while being read: the last reader frees the arrays
+    int fin_word = -1;        // CONTINUOUS: completion word of its construct-then-operate piece
+    uint64_t fin_step = 0;    // the step that holds that piece
 };
 
 bool has_y(int op) { return op == SX_OP_ADD || op == SX_OP_TRIAD; }
@@ -114,6 +120,12 @@ struct sx_server {
     // step number to, and one device counter of finished blocks per slot
     unsigned long long *done_host = nullptr, *done_dev = nullptr;
     unsigned int *counters = nullptr;
+    // completion words of construct-then-operate pieces (host-mapped, set to 1 by the device) with
+    // their device tile counters; words in use are watched through fin_watch (server thread only)
+    unsigned long long *fin_host = nullptr, *fin_dev = nullptr;
+    unsigned int *fin_count = nullptr;
+    std::vector<int> free_fin;
+    std::vector<Request *> fin_watch;
     std::vector<int> free_slots;
     std::vector<cudaEvent_t> free_events;
     uint64_t next_id = 1;
@@ -151,6 +163,14 @@ bool step_reported(const sx_server *s, uint64_t seq) {
 // request keeps its memory for long, and without the cap a handful of them could fill the
 // arena and stall every admission behind them.
 constexpr int kMaxLarge = 4;
+
+// Completion words for construct-then-operate pieces in flight (more such pieces wait for their
+// step to retire instead).
+constexpr int kFinWords = 4096;
+
+bool fin_reported(const sx_server *s, const Request *q) {
+    return ((volatile unsigned long long *)s->fin_host)[q->fin_word] != 0;
+}
 
 bool is_large(const sx_server *s, const Request *q) {
     return (q->bytes[0] + q->bytes[1] + q->bytes[2]) * 16 > s->arena->size();
@@ -254,62 +274,98 @@ int enqueue_fifo(sx_server *s, Request *q, Step &st) {
 int launch_step(sx_server *s, bool *launched) {
     TraceRange tr("sx_server step");
     *launched = false;
+    const uint64_t budget = (uint64_t)(uint32_t)s->cfg.chunk_bytes;
     std::vector<sched::Want> w;
     std::vector<Request *> by_key;
+    std::vector<uint8_t> whole;  // short and not started: planned with the bytes of both phases
     for (Request *q : s->active) {
         if (q->phase >= 2) continue;
-        const uint64_t later = q->phase == 0 ? (uint64_t)q->r.n * phase_bytes_per_elem(*q, 1) : 0;
-        w.push_back({by_key.size(), q->admit_seq, phase_bytes_per_elem(*q, q->phase), q->r.n - q->next, later});
+        const uint64_t p0 = phase_bytes_per_elem(*q, 0), p1 = phase_bytes_per_elem(*q, 1);
+        const bool short_whole = q->phase == 0 && q->next == 0 && (uint64_t)q->r.n * (p0 + p1) <= budget / 4;
+        const uint64_t later = q->phase == 0 && !short_whole ? (uint64_t)q->r.n * p1 : 0;
+        const uint64_t per = short_whole ? p0 + p1 : phase_bytes_per_elem(*q, q->phase);
+        w.push_back({by_key.size(), q->admit_seq, per, q->r.n - q->next, later});
         by_key.push_back(q);
+        whole.push_back(short_whole ? 1 : 0);
     }
     if (w.empty()) return SX_OK;
     // elements of each request's current phase in this step, in the policy's order (sx_sched.h)
-    const std::vector<uint64_t> grant = sched::plan_step(s->cfg.policy, (uint64_t)(uint32_t)s->cfg.chunk_bytes, w);
+    const std::vector<uint64_t> grant = sched::plan_step(s->cfg.policy, budget, w);
     const int slot = s->free_slots.back();
     s->free_slots.pop_back();
-    std::vector<sx_batch_item> items;
-    std::vector<uint8_t> dep;  // operation pieces whose inputs come from a step still in flight
+    std::vector<StepItem> items;
     Step st;
     st.slot = slot;
     st.seq = s->step_seq + 1;
+    std::vector<Request *> watch;  // requests given a completion word in this step
     for (size_t i = 0; i < w.size(); ++i) {
         if (grant[i] == 0) continue;
         Request *q = by_key[w[i].key];
         q->last_step = st.seq;
-        const uint64_t per = phase_bytes_per_elem(*q, q->phase);
         const uint64_t elems = grant[i];
         const uint64_t lo = q->next, hi = lo + elems;
         const sx_request &r = q->r;
         const size_t es = dtype_size(r.dtype);
+        if (whole[w[i].key] && elems == r.n) {
+            // the whole request in one piece: construct x (and y), then the operation
+            StepItem si;
+            si.item.op = r.op;
+            si.item.dtype = r.dtype;
+            si.item.n = r.n;
+            si.item.x = ptr_of(s, q, 0);
+            si.item.y = ptr_of(s, q, 1);
+            si.item.out = ptr_of(s, q, 2);
+            si.item.q = r.q;
+            si.item.q2 = r.lo;
+            si.item.seed = r.seed_x;
+            si.item.index_base = 0;
+            si.flags = kStepConstructThenOp;
+            si.seed2 = r.seed_y;
+            si.hi = r.hi;
+            if (!s->free_fin.empty()) {
+                q->fin_word = s->free_fin.back();
+                s->free_fin.pop_back();
+                ((volatile unsigned long long *)s->fin_host)[q->fin_word] = 0;
+                q->fin_step = st.seq;
+                si.fin_word = (uint32_t)q->fin_word + 1;
+                watch.push_back(q);
+            }
+            items.push_back(si);
+            st.bytes += (uint64_t)r.n * (phase_bytes_per_elem(*q, 0) + phase_bytes_per_elem(*q, 1));
+            q->phase = 2;
+            st.finishing.push_back(q);
+            s->stats.fused++;
+            continue;
+        }
+        const uint64_t per = phase_bytes_per_elem(*q, q->phase);
         if (q->phase == 0) {
-            sx_batch_item it{};
-            it.op = SX_OP_SEED;
-            it.dtype = r.dtype;
-            it.n = elems;
-            it.out = (char *)ptr_of(s, q, 0) + lo * es;
-            it.q = r.lo;
-            it.q2 = r.hi;
-            it.seed = r.seed_x;
-            it.index_base = lo;
-            items.push_back(it);
-            dep.push_back(0);
+            StepItem si;
+            si.item.op = SX_OP_SEED;
+            si.item.dtype = r.dtype;
+            si.item.n = elems;
+            si.item.out = (char *)ptr_of(s, q, 0) + lo * es;
+            si.item.q = r.lo;
+            si.item.q2 = r.hi;
+            si.item.seed = r.seed_x;
+            si.item.index_base = lo;
+            items.push_back(si);
             if (has_y(r.op)) {
-                it.out = (char *)ptr_of(s, q, 1) + lo * es;
-                it.seed = r.seed_y;
-                items.push_back(it);
-                dep.push_back(0);
+                si.item.out = (char *)ptr_of(s, q, 1) + lo * es;
+                si.item.seed = r.seed_y;
+                items.push_back(si);
             }
         } else {
-            sx_batch_item it{};
-            it.op = r.op;
-            it.dtype = r.dtype;
-            it.n = elems;
-            it.x = (const char *)ptr_of(s, q, 0) + lo * es;
-            it.y = has_y(r.op) ? (const char *)ptr_of(s, q, 1) + lo * es : nullptr;
-            it.out = (char *)ptr_of(s, q, 2) + lo * es;
-            it.q = r.q;
-            items.push_back(it);
-            dep.push_back(q->inputs_step > s->retired_seq ? 1 : 0);
+            StepItem si;
+            si.item.op = r.op;
+            si.item.dtype = r.dtype;
+            si.item.n = elems;
+            si.item.x = (const char *)ptr_of(s, q, 0) + lo * es;
+            si.item.y = has_y(r.op) ? (const char *)ptr_of(s, q, 1) + lo * es : nullptr;
+            si.item.out = (char *)ptr_of(s, q, 2) + lo * es;
+            si.item.q = r.q;
+            // operation pieces whose inputs come from a step still in flight wait for it
+            si.flags = q->inputs_step > s->retired_seq ? kStepDependent : 0u;
+            items.push_back(si);
         }
         st.bytes += elems * per;
         q->next = hi;
@@ -320,25 +376,23 @@ int launch_step(sx_server *s, bool *launched) {
             if (q->phase == 2) st.finishing.push_back(q);
         }
     }
-    // independent pieces first, so that blocks reach the ones that must wait as late as possible
-    std::vector<size_t> order(items.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&dep](size_t a, size_t b) { return dep[a] < dep[b]; });
-    std::vector<sx_batch_item> sorted(items.size());
-    std::vector<uint8_t> sdep(items.size());
-    for (size_t i = 0; i < order.size(); ++i) {
-        sorted[i] = items[order[i]];
-        sdep[i] = dep[order[i]];
-    }
-    items.swap(sorted);
-    dep.swap(sdep);
-    const StepReport report{st.seq, s->done_dev, s->counters + slot};
+    // independent pieces first (in the policy's order), so that blocks reach the ones that must
+    // wait as late as possible
+    std::stable_sort(items.begin(), items.end(), [](const StepItem &a, const StepItem &b) {
+        return (a.flags & kStepDependent) < (b.flags & kStepDependent);
+    });
+    const StepReport report{st.seq, s->done_dev, s->counters + slot, s->fin_dev, s->fin_count};
     const int rc = step_launch(s->t, s->t->stream, s->slots[slot], items.data(), items.size(), s->kcfg,
-                               dep.data(), s->cfg.serialize_steps == 0, &report);
+                               s->cfg.serialize_steps == 0, &report);
     if (rc != SX_OK) {
         s->free_slots.push_back(slot);
+        for (Request *q : watch) {
+            s->free_fin.push_back(q->fin_word);
+            q->fin_word = -1;
+        }
         return rc;
     }
+    for (Request *q : watch) s->fin_watch.push_back(q);
     st.t_launch = now_seconds();
     s->step_seq = st.seq;
     s->inflight.push_back(std::move(st));
@@ -356,6 +410,53 @@ void finalize_cancel(sx_server *s, Request *q) {
     s->stats.cancelled++;
     s->admit_dirty = true;
     s->arrivals.fetch_add(1, std::memory_order_release);
+}
+
+// Stop watching q's completion word and give the word back.
+void unwatch(sx_server *s, Request *q) {
+    s->fin_watch.erase(std::find(s->fin_watch.begin(), s->fin_watch.end(), q));
+    s->free_fin.push_back(q->fin_word);
+    q->fin_word = -1;
+}
+
+// True if a watched construct-then-operate piece has reported (server thread, lock not needed).
+bool any_fin_reported(const sx_server *s) {
+    for (const Request *q : s->fin_watch)
+        if (fin_reported(s, q)) return true;
+    return false;
+}
+
+// Requests whose construct-then-operate piece has reported are DONE (or CANCELLED) at once, while
+// the rest of their step may still run: their tiles are all done, and no other piece touches
+// their arrays.  Returns true if any completed.
+bool collect_reported(sx_server *s) {
+    bool any = false;
+    for (size_t i = 0; i < s->fin_watch.size();) {
+        Request *q = s->fin_watch[i];
+        if (!fin_reported(s, q)) {
+            ++i;
+            continue;
+        }
+        unwatch(s, q);  // removes s->fin_watch[i]
+        for (Step &st : s->inflight) {
+            if (st.seq != q->fin_step) continue;
+            st.finishing.erase(std::find(st.finishing.begin(), st.finishing.end(), q));
+            break;
+        }
+        s->stats.early_done++;
+        s->active.erase(std::find(s->active.begin(), s->active.end(), q));
+        if (q->cancel) {
+            finalize_cancel(s, q);
+        } else {
+            q->state = SX_REQ_DONE;
+            q->t_done = now_seconds();
+            s->stats.completed++;
+            if (q->r.flags & SX_REQ_AUTO_RELEASE) release_arrays(s, q);
+            s->admit_dirty = true;
+        }
+        any = true;
+    }
+    return any;
 }
 
 // Retire completed steps from the front of the in-flight queue.  Returns true if any retired
@@ -381,6 +482,7 @@ bool retire(sx_server *s) {
         }
         const double now = now_seconds();
         for (Request *q : st.finishing) {
+            if (q->fin_word >= 0) unwatch(s, q);  // its word was not seen before the step retired
             s->active.erase(std::find(s->active.begin(), s->active.end(), q));
             if (q->cancel) {
                 finalize_cancel(s, q);
@@ -417,7 +519,7 @@ void server_loop(sx_server *s) {
     std::unique_lock<std::mutex> lk(s->mu);
     const bool fifo = s->cfg.mode == SX_SERVE_FIFO;
     for (;;) {
-        const bool retired = retire(s);
+        const bool retired = retire(s) | collect_reported(s);
         if (retired) s->done_cv.notify_all();
         if (!s->stop) admit(s);
         bool launched = false;
@@ -495,7 +597,7 @@ void server_loop(sx_server *s) {
             lk.unlock();
             const double spin_until = now_seconds() + 5e-4;
             while (!(by_word ? step_reported(s, want) : cudaEventQuery(ev) != cudaErrorNotReady) &&
-                   s->arrivals.load(std::memory_order_acquire) == seen) {
+                   s->arrivals.load(std::memory_order_acquire) == seen && !any_fin_reported(s)) {
                 if (now_seconds() < spin_until) std::this_thread::yield();
                 else std::this_thread::sleep_for(std::chrono::microseconds(20));
             }
@@ -648,28 +750,37 @@ int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out) {
     if (c.mode == SX_SERVE_CONTINUOUS) {
         s->slots.resize(c.steps_in_flight);
         for (int i = c.steps_in_flight - 1; i >= 0; --i) s->free_slots.push_back(i);
+        auto undo = [s, t, &c]() {
+            if (s->done_host) cudaFreeHost(s->done_host);
+            if (s->counters) cudaFree(s->counters);
+            if (s->fin_host) cudaFreeHost(s->fin_host);
+            if (s->fin_count) cudaFree(s->fin_count);
+            cudaStreamDestroy(s->read_stream);
+            cudaFree(s->base);
+            t->used -= c.budget_bytes;
+            delete s;
+        };
         cudaError_t e2 = cudaHostAlloc((void **)&s->done_host, sizeof(unsigned long long), cudaHostAllocMapped);
         if (e2 == cudaSuccess) e2 = cudaHostGetDevicePointer((void **)&s->done_dev, s->done_host, 0);
         if (e2 == cudaSuccess) e2 = cudaMalloc(&s->counters, c.steps_in_flight * sizeof(unsigned int));
         if (e2 == cudaSuccess) e2 = cudaMemset(s->counters, 0, c.steps_in_flight * sizeof(unsigned int));
+        if (e2 == cudaSuccess)
+            e2 = cudaHostAlloc((void **)&s->fin_host, kFinWords * sizeof(unsigned long long), cudaHostAllocMapped);
+        if (e2 == cudaSuccess) e2 = cudaHostGetDevicePointer((void **)&s->fin_dev, s->fin_host, 0);
+        if (e2 == cudaSuccess) e2 = cudaMalloc(&s->fin_count, kFinWords * sizeof(unsigned int));
+        if (e2 == cudaSuccess) e2 = cudaMemset(s->fin_count, 0, kFinWords * sizeof(unsigned int));
         if (e2 != cudaSuccess) {
-            if (s->done_host) cudaFreeHost(s->done_host);
-            if (s->counters) cudaFree(s->counters);
-            cudaStreamDestroy(s->read_stream);
-            cudaFree(s->base);
-            t->used -= c.budget_bytes;
-            delete s;
+            undo();
             return cuda_fail(e2, "server step reports");
         }
         *(volatile unsigned long long *)s->done_host = 0;
+        for (int i = kFinWords - 1; i >= 0; --i) {
+            ((volatile unsigned long long *)s->fin_host)[i] = 0;
+            s->free_fin.push_back(i);
+        }
         const int rc = step_warm(t->stream);
         if (rc != SX_OK) {
-            cudaFreeHost(s->done_host);
-            cudaFree(s->counters);
-            cudaStreamDestroy(s->read_stream);
-            cudaFree(s->base);
-            t->used -= c.budget_bytes;
-            delete s;
+            undo();
             return rc;
         }
     }
@@ -902,6 +1013,8 @@ int sx_server_destroy(sx_server *s) {
         for (auto &sl : s->slots) step_slot_free(sl);
         if (s->done_host) cudaFreeHost(s->done_host);
         if (s->counters) cudaFree(s->counters);
+        if (s->fin_host) cudaFreeHost(s->fin_host);
+        if (s->fin_count) cudaFree(s->fin_count);
         for (auto ev : s->free_events) cudaEventDestroy(ev);
         if (s->read_stream) cudaStreamDestroy(s->read_stream);
         cudaFree(s->base);

@@ -30,7 +30,7 @@ SX_SERVE_CONTINUOUS, SX_SERVE_FIFO = 0, 1
 SX_SERVE_POLICY_SRPT, SX_SERVE_POLICY_FAIR, SX_SERVE_POLICY_SHORT_FIRST = 0, 1, 2
 SX_REQ_QUEUED, SX_REQ_ACTIVE, SX_REQ_DONE, SX_REQ_REJECTED, SX_REQ_RELEASED, SX_REQ_CANCELLED = 0, 1, 2, 3, 4, 5
 SX_REQ_AUTO_RELEASE = 1
-SX_NOALLOC_MAX_ITEMS, SX_NOALLOC_MAX_TILES, SX_NOALLOC_SCRATCH_BYTES = 4096, 65536, 884736
+SX_NOALLOC_MAX_ITEMS, SX_NOALLOC_MAX_TILES, SX_NOALLOC_SCRATCH_BYTES = 4096, 65536, 950272
 
 OPS = {"copy": SX_OP_COPY, "scale": SX_OP_SCALE, "add": SX_OP_ADD, "triad": SX_OP_TRIAD,
        "seed": SX_OP_SEED}
@@ -99,7 +99,7 @@ class sx_server_stats(C.Structure):
                                           "steps", "launches", "bytes_moved", "arena_used",
                                           "arena_peak", "arena_bytes")] + [(n, C.c_double) for n in (
                                               "busy_seconds", "host_step_seconds", "host_admit_seconds")] + [
-        ("cancelled", C.c_uint64)]
+        ("cancelled", C.c_uint64), ("fused", C.c_uint64), ("early_done", C.c_uint64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

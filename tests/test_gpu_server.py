@@ -80,6 +80,42 @@ def test_mix_equals_alone(target, mode):
     sx.sx_server_destroy(s)
 
 
+def test_short_requests_run_whole_and_report_early(target):
+    """Requests whose whole work fits a quarter of the step budget run as one construct-then-
+    operate piece and complete from that piece's own report, while the long request sharing their
+    steps goes on; longer ones run in two phases.  Every result is the oracle's."""
+    s = sx.sx_server_create(target, budget_bytes=8 << 30, chunk_bytes=1 << 30)
+    long_r = dict(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=1 << 27, q=3.0, seed_x=91, seed_y=92,
+                  lo=-1.0, hi=1.0)  # 5 GiB of work: several 1 GiB steps of ~0.15 ms
+    mid_r = dict(op=sx.SX_OP_ADD, dtype=sx.SX_F32, n=20 << 20, q=1.0, seed_x=93, seed_y=94,
+                 lo=-2.0, hi=0.5)  # 400 MiB of work: over a quarter of the budget, two phases
+    shorts = [dict(op=[sx.SX_OP_COPY, sx.SX_OP_SCALE, sx.SX_OP_ADD, sx.SX_OP_TRIAD][k % 4],
+                   dtype=sx.SX_F64 if k % 2 else sx.SX_F32, n=(1 << 14) + 37 * k, q=-0.5,
+                   seed_x=200 + k, seed_y=300 + k, lo=-1.0, hi=1.0) for k in range(16)]
+    lid = sx.sx_server_submit(s, **long_r)
+    mid = sx.sx_server_submit(s, **mid_r)
+    sids = [sx.sx_server_submit(s, **r) for r in shorts]
+    _check_all(s, sids + [mid, lid], shorts + [mid_r, long_r], "short and long")
+    st = sx.sx_server_stats_get(s)
+    assert st["fused"] == len(shorts), st
+    assert 1 <= st["early_done"] <= st["fused"], st
+    sx.sx_server_destroy(s)
+
+
+def test_fused_requests_with_a_general_range(target):
+    """A construct-then-operate piece builds its inputs over any [lo, hi) in both types, in one
+    tile or in several (16 KiB tiles: a 4097-element FP64 triad is 11 tiles)."""
+    reqs = [dict(op=op, dtype=dt, n=n, q=2.5, seed_x=7 + n, seed_y=8 + n, lo=-3.0, hi=5.5)
+            for op in (sx.SX_OP_SCALE, sx.SX_OP_TRIAD) for dt in (sx.SX_F64, sx.SX_F32)
+            for n in (1, 63, 4097)]
+    for tile in (0, 16384):
+        s = sx.sx_server_create(target, budget_bytes=1 << 30, chunk_bytes=1 << 20, tile_bytes=tile)
+        ids = [sx.sx_server_submit(s, **r) for r in reqs]
+        _check_all(s, ids, reqs, f"tile {tile}")
+        assert sx.sx_server_stats_get(s)["fused"] == len(reqs)
+        sx.sx_server_destroy(s)
+
+
 def test_replayed_poisson_stream(target):
     reqs = _requests(150, seed=5)
     arr = si.poisson_requests(5, 150, rate_per_s=20000.0)
