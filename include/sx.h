@@ -390,10 +390,13 @@ typedef struct sx_server sx_server;
 /* Modes.  CONTINUOUS: the server thread runs "steps"; each step is one launch of the batched
  * kernel holding a piece of every active request's current phase (inputs construction, then the
  * operation), the step's byte budget shared out so that short requests finish in one step and
- * long ones share the rest.  Requests that arrive while steps are on the GPU are admitted as
- * slots and arena memory free up and join the next step.  FIFO: the per-call baseline; each
- * admitted request is enqueued at once as its own launches (construct x, construct y, op) on
- * the stream, in arrival order. */
+ * long ones share the rest.  A request whose whole work is at most a quarter of the budget, taken
+ * whole by a step, runs as one piece that constructs its inputs and then applies the operation
+ * tile by tile, and is DONE as soon as that piece's last tile has finished (the device sets a
+ * completion word), before the rest of the step.  Requests that arrive while steps are on the
+ * GPU are admitted as slots and arena memory free up and join the next step.  FIFO: the
+ * per-call baseline; each admitted request is enqueued at once as its own launches (construct x,
+ * construct y, op) on the stream, in arrival order. */
 enum { SX_SERVE_CONTINUOUS = 0, SX_SERVE_FIFO = 1 };
 typedef struct sx_server_cfg {
     uint64_t budget_bytes;   /* device arena the server allocates once; admission bound.  Large
