@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsx.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["sx_runtime.cpp", "sx_kernels.cu", "sx_bulk.cu", "sx_batch.cu", "sx_tune.cpp",
+SOURCES = ["sx_runtime.cpp", "sx_kernels.cu", "sx_seed.cu", "sx_bulk.cu", "sx_batch.cu", "sx_tune.cpp",
            "sx_server.cpp", "sx_selftest.cu", "sx_jit.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",

@@ -19,6 +19,7 @@
 
 #include "sx_device.cuh"
 #include "sx_internal.h"
+#include "sx_seed.cuh"
 
 namespace sx {
 namespace {

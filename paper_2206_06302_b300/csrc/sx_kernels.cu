@@ -218,34 +218,6 @@ int dispatch_op(const sx_target *t, cudaStream_t s, int op, const void *x, const
     }
 }
 
-// ---- seeded bulk construction ---------------------------------------------------------------
-// All threads of the grid share the range (seed_range); PM1: lo = -1, hi = 1 in binary64.
-template <class T, bool PM1>
-__global__ void __launch_bounds__(256) k_seed(T *out, uint64_t n, uint64_t seed, T lo, T span, uint64_t base) {
-    seed_range<T, PM1>(out, n, seed, base, lo, span, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                       (uint64_t)gridDim.x * blockDim.x);
-}
-
-// Blocks of 256 threads for `n` elements taken `per_thread` at a time: up to 8 per SM.
-unsigned seed_blocks(size_t n, int per_thread) {
-    uint64_t b = (n + 256ull * per_thread - 1) / (256ull * per_thread);
-    if (b > 148ull * 8) b = 148ull * 8;
-    return b == 0 ? 1u : (unsigned)b;
-}
-
-template <class T>
-__global__ void k_fill(T *out, uint64_t n, T v) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = v;
-}
-
-unsigned setup_blocks(size_t n) {
-    uint64_t b = (n + 255) / 256;
-    if (b > 148ull * 32) b = 148ull * 32;
-    return b == 0 ? 1u : (unsigned)b;
-}
-
 // ---- fused STREAM passes ---------------------------------------------------------------------
 // Element i's chain of roundings over `iters` passes depends only on a[i]: Copy sets c=a,
 // Scale b=RN(c*q), Add c=RN(a+b), Triad a=RN(b+RN(c*q)).  One kernel can run the whole chain
@@ -351,38 +323,6 @@ int launch_stream_op(const sx_target *t, cudaStream_t s, int op, int dtype, cons
     if (dtype == SX_F64) return dispatch_op<double>(t, s, op, x, y, out, n, q, c);
     if (dtype == SX_F32) return dispatch_op<float>(t, s, op, x, y, out, n, q, c);
     return fail(SX_ERR_DTYPE, "STREAM kernels take F32 or F64 (got dtype %d)", dtype);
-}
-
-int launch_fill(cudaStream_t s, int dtype, void *out, size_t n, double value) {
-    if (n == 0) return SX_OK;
-    const unsigned b = setup_blocks(n);
-    if (dtype == SX_F64) k_fill<double><<<b, 256, 0, s>>>((double *)out, n, value);
-    else if (dtype == SX_F32) k_fill<float><<<b, 256, 0, s>>>((float *)out, n, (float)value);
-    else if (dtype == SX_U8) k_fill<uint8_t><<<b, 256, 0, s>>>((uint8_t *)out, n, (uint8_t)value);
-    else return fail(SX_ERR_DTYPE, "bulk_construct: unsupported dtype %d", dtype);
-    SX_CUDA(cudaGetLastError());
-    return SX_OK;
-}
-
-int launch_seed(cudaStream_t s, int dtype, void *out, size_t n, uint64_t seed, double lo, double hi,
-                uint64_t index_base) {
-    if (n == 0) return SX_OK;
-    if (dtype == SX_F64) {
-        const double span = hi - lo;
-        const unsigned b = seed_blocks(n, 8);
-        if (lo == -1.0 && hi == 1.0)
-            k_seed<double, true><<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
-        else
-            k_seed<double, false><<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
-    } else if (dtype == SX_F32) {
-        const float lo32 = (float)lo, hi32 = (float)hi;
-        const float span = hi32 - lo32;
-        k_seed<float, false><<<seed_blocks(n, 16), 256, 0, s>>>((float *)out, n, seed, lo32, span, index_base);
-    } else {
-        return fail(SX_ERR_DTYPE, "seed_uniform takes F32 or F64 (got dtype %d)", dtype);
-    }
-    SX_CUDA(cudaGetLastError());
-    return SX_OK;
 }
 
 int launch_stream_fused(const sx_target *t, cudaStream_t s, int dtype, void *a, void *b, void *c,

@@ -404,6 +404,32 @@ def _small_k_indices(seed, count):
     return np.nonzero(np.abs(k) < (1 << 32))[0]
 
 
+def test_seeded_general_range_on_both_units(target):
+    """A general [lo, hi) in binary64 takes three of every four elements through an integer-unit form
+    (u assembled from the word's bits, the product by mul_rn_int; a short-significand span takes
+    its short path).  Words with M = w >> 11 below 2^32 (u < 2^-21, found by the host generator)
+    put the leading bit in the low half; at every 8-byte offset each such word meets both forms.
+    Spans: long and short significands, negative, huge and tiny (products near the subnormal and
+    overflow ends defer to the FP64 pipe)."""
+    import torch
+    seed, count = 777, 1 << 23
+    w = si.words(seed, count)
+    hits = np.nonzero((w >> np.uint64(11)) < np.uint64(1 << 32))[0]
+    assert hits.size >= 2, "no small word in range"
+    n = int(hits[-1]) + 8
+    buf = torch.zeros(8 * n + 64, dtype=torch.uint8, device="cuda")
+    ranges = [(0.25, 7.5), (-3.0, 0.1), (1.0, 1.0 + 2.0 ** -40), (5.0, -2.0),
+              (-1.0e300, 1.0e300), (0.0, 2.0 ** -1000), (-1.0, 0.5), (1.0e-310, 3.0e-310)]
+    for off in (0, 8, 16, 24):
+        for lo, hi in ranges:
+            d = sx.sx_array_wrap(target, sx.SX_F64, buf.data_ptr() + off, n)
+            sx.sx_seed_uniform(d, seed, lo, hi)
+            got = to_host(d)
+            want = si.uniform(seed, n, np.float64, lo, hi)
+            assert_bitwise(got, want, f"[{lo}, {hi}) at offset {off}")
+            sx.sx_free(d)
+
+
 def test_seeded_pm1_small_magnitudes(target):
     """The lo = -1, hi = 1 binary64 construction has a separate path for |k| < 2^32 (about one
     word in 2^20): such words, found by the host generator, must come out exact through the
