@@ -135,3 +135,33 @@ def test_cpp_layer_compiles_and_links(tmp_path):
         pytest.skip("a GPU is present: the GPU test runs the client")
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 2 and "no device" in r.stderr, (r.returncode, r.stderr)
+
+
+STRUCTS = ["sx_launch_cfg", "sx_target_info", "sx_batch_item", "sx_batch_cfg", "sx_server_cfg",
+           "sx_request", "sx_request_status", "sx_server_stats"]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every public struct of the binding has the header's size and field offsets (a C program
+    compiled against sx.h prints them), so a field added on one side only is caught."""
+    import ctypes
+    from paper_2206_06302_b300 import sx as binding
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sx.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(binding, name)
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe)], check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name in STRUCTS:
+        cls = getattr(binding, name)
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
