@@ -165,3 +165,25 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_shipped_tune_table_is_complete_and_valid():
+    """The tuner table shipped with the package holds one entry per STREAM kernel, type and log2
+    size from 2^16 to 2^29, each a launch shape the library accepts (checked on the host)."""
+    import json
+    path = os.path.join(ROOT, "paper_2206_06302_b300", "tune_b300.json")
+    entries = json.load(open(path))["ops"]
+    keys = {(e["op"], e["dtype"], e["bucket"]) for e in entries}
+    assert len(keys) == len(entries) == 4 * 2 * 14
+    assert keys == {(op, dt, b) for op in range(4) for dt in (1, 2) for b in range(16, 30)}
+    for e in entries:
+        assert e["variant"] in (1, 2, 3, 4), e
+        assert e["threads"] % 32 == 0 and 32 <= e["threads"] <= 1024, e
+        assert e["fp64_mul"] in (0, 1, 2), e
+        if e["variant"] == 1:
+            assert e["vec_bytes"] in (16, 32) and e["unroll"] in (1, 2, 4), e
+            assert e["cache_hint"] in (0, 1) and 0 <= e["blocks_per_sm"] <= 64, e
+        else:
+            assert e["tile_bytes"] % 1024 == 0 and 1024 <= e["tile_bytes"] <= 65536, e
+            assert 2 <= e["stages"] <= 8 and 1 <= e["blocks_per_sm"] <= 4, e
+            assert e["threads"] >= (96 if e["variant"] in (3, 4) else 64), e
