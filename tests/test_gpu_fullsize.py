@@ -84,9 +84,18 @@ def test_beyond_32bit_indices_fp32(target, op):
     torch.cuda.empty_cache()
 
 
+FAMILIES = {"auto": None,
+            "bulk": dict(variant=sx.SX_VARIANT_BULK, fp64_mul=2),
+            "tma": dict(variant=sx.SX_VARIANT_TMA, fp64_mul=2),
+            "tma_tensor": dict(variant=sx.SX_VARIANT_TMA_TENSOR, fp64_mul=2)}
+
+
+@pytest.mark.parametrize("family", list(FAMILIES))
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
-def test_largest_sweep_size_ragged(target, dt):
-    """The sweep's largest size plus a ragged tail, every kernel in the bench's launch shapes."""
+def test_largest_sweep_size_ragged(target, dt, family):
+    """The sweep's largest size plus a ragged tail, every kernel, in the bench's launch shapes
+    (auto) and in each bulk-copy family's default shape: persistent blocks walk thousands of
+    tiles, and the tensor-map view has 2^21 rows."""
     import torch
     n = (1 << 29) + 7
     tdt = torch.float64 if dt == np.float64 else torch.float32
@@ -96,14 +105,14 @@ def test_largest_sweep_size_ragged(target, dt):
     x, y, o = (sx.sx_array_wrap(target, code, b.data_ptr(), n) for b in bufs)
     sx.sx_seed_uniform(x, 41, -1.0, 1.0)
     sx.sx_seed_uniform(y, 42, -1.0, 1.0)
-    e = sx.sx_executor_create(target, sx.SX_PAR)
+    e = sx.sx_executor_create(target, sx.SX_PAR, FAMILIES[family])
     idx = np.unique(np.concatenate([np.arange(0, 64), np.arange(n - 300, n),
                                     np.random.default_rng(2).integers(0, n, 1 << 16)]))
     xs = si.uniform_at(41, idx.astype(np.uint64), dt)
     ys = si.uniform_at(42, idx.astype(np.uint64), dt)
     for name, op in (("copy", 0), ("scale", 1), ("add", 2), ("triad", 3)):
         sx.sx_execute(e, op, x, y, o, 3.0)
-        assert_bitwise(_sampled(torch, bufs[2], idx), oracle.apply(name, xs, ys, 3.0), name)
+        assert_bitwise(_sampled(torch, bufs[2], idx), oracle.apply(name, xs, ys, 3.0), f"{name} {family}")
     for a in (x, y, o):
         sx.sx_free(a)
     sx.sx_executor_destroy(e)
