@@ -723,6 +723,7 @@ def run_sweep(args):
                            tile_bytes=16384, stages=3, fp64_mul=2),
     }
     execs = {k: sx.sx_executor_create(t, sx.SX_PAR_TASK, v) for k, v in shapes.items()}
+    l2 = sx.sx_target_info_get(t)["l2_bytes"]  # the regime split: the kernel's arrays fit in L2 or not
     ops = (("copy", sx.SX_OP_COPY, 2), ("scale", sx.SX_OP_SCALE, 2), ("add", sx.SX_OP_ADD, 3),
            ("triad", sx.SX_OP_TRIAD, 3))
     rows = []
@@ -750,14 +751,16 @@ def run_sweep(args):
                     ev1.synchronize()
                     ms = ev0.elapsed_time(ev1) / reps
                     rows.append({"dtype": dname, "log2n": lg, "op": name, "variant": vname,
+                                 "regime": "L2-resident" if nbytes <= l2 else "HBM",
                                  "us": round(ms * 1e3, 2), "GB/s": round(nbytes / (ms * 1e-3) / 1e9, 1)})
             for v in views:
                 sx.sx_free(v)
         for a in arrs:
             sx.sx_free(a)
     sx.sx_target_synchronize(t)
-    print(json.dumps({"sweep": rows, "shapes": shapes,
-                      "note": "per-launch device time, back-to-back launches on the same arrays"}),
+    print(json.dumps({"sweep": rows, "shapes": shapes, "l2_bytes": l2,
+                      "note": "per-launch device time, back-to-back launches on the same arrays; "
+                              "regime: the kernel's arrays together fit in L2 or not"}),
           flush=True)
     return 0
 
