@@ -186,7 +186,7 @@ def run_reference(args):
         "config": {"workload": f"STREAM FP64 pass (copy,scale,add,triad), q=3, bounded sample "
                                f"n={n} per array of the n=2^27 workload", "n": n},
         "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"n={n} FP64 per array, {args.steps} passes"},
+                         "sample": f"n={n} FP64 per array, {args.steps} passes", "cpu": _cpu_model()},
         "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -657,6 +657,19 @@ def copies_section(sx, torch, t, device=0, sizes=(1 << 20, 1 << 24, 1 << 28, 1 <
                     "at once on two streams (pinned); best of %d, host clock" % reps, "runs": rows}
 
 
+def _cpu_model() -> str:
+    """The host CPU's model name (Linux /proc/cpuinfo), for the CPU baselines."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
+
+
 def cpu_oracle_threads_gbs(n: int, seconds: float):
     """The oracle's STREAM pass with its loops block-partitioned over the host cores: thread k
     runs the oracle on elements [n k / T, n (k + 1) / T) of each array, pinned to one core; a pass
@@ -926,13 +939,13 @@ def run_ours(args):
         gbs, passes, el = cpu_oracle_gbs(args.cpu_n, args.cpu_seconds)
         cpu = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"STREAM FP64 pass on n={args.cpu_n} per array, {passes} passes "
-                         f"in {el:.1f} s (serial C, -O2 -ffp-contract=off)"}
+                         f"in {el:.1f} s (serial C, -O2 -ffp-contract=off)", "cpu": _cpu_model()}
         if args.cpu_threads_n:
             gbs, passes, el, nt = cpu_oracle_threads_gbs(args.cpu_threads_n, args.cpu_seconds / 2)
             extra["cpu_baseline_threads"] = {
                 "value": round(gbs, 3), "unit": "GB/s", "cores": nt, "kind": "oracle loops, block-partitioned",
                 "sample": f"STREAM FP64 pass on n={args.cpu_threads_n} per array, {passes} passes in "
-                          f"{el:.1f} s, one contiguous block per pinned thread"}
+                          f"{el:.1f} s, one contiguous block per pinned thread", "cpu": _cpu_model()}
 
     triad_ms = per["triad"] / args.steps
     achieved = 3 * n * es / (triad_ms * 1e-3) / 1e9
