@@ -1,10 +1,11 @@
 /*
  * sx.hpp -- header-only C++17 layer over the C ABI (sx.h), in the shape of the paper's programming
  * model: a target (Section 3.1), an allocator that places arrays on a target and constructs them
- * there in bulk (Section 3.2, Listing 1), an executor (Section 3.3, Listing 2), and copy/transform
- * algorithms taking a parallel policy bound to an executor, par.on(exec) (Section 3.4, Listing 3),
- * enough to write STREAM as Section 5 does.  Every call goes to libsx; failures throw sx::error.
- * Handles are move-only and released in their destructors.
+ * there in bulk (Section 3.2, Listing 1), an executor with async_execute returning a future and a
+ * bulk executor with bulk_async_execute (Section 3.3, Listing 2), and copy/transform algorithms
+ * taking a parallel policy bound to an executor, par.on(exec) (Section 3.4, Listing 3), enough to
+ * write STREAM as Section 5 does.  Every call goes to libsx; failures throw sx::error.  Handles are
+ * move-only and released in their destructors.
  */
 #ifndef SX_HPP_
 #define SX_HPP_
@@ -115,6 +116,12 @@ class vector {
 
     size_t size() const noexcept { return n_; }
     sx_array *get() const noexcept { return a_; }
+    // The elements' device address (for batch items and interoperation).
+    T *data() const {
+        void *p = nullptr;
+        check(sx_array_data(a_, &p, nullptr, nullptr), "sx_array_data");
+        return static_cast<T *>(p);
+    }
     const allocator<T> &get_allocator() const noexcept { return alloc_; }
     // Seeded uniform values in [lo, hi) (sx_seed_uniform), constructed on the device.
     void seed_uniform(uint64_t seed, double lo = -1.0, double hi = 1.0) {
@@ -146,6 +153,76 @@ class executor {
 
   private:
     sx_executor *e_ = nullptr;
+};
+
+// The result of asynchronous work (Listing 2's future): wait() blocks until the work is done and
+// rethrows its failure; elapsed_ms() is its device time.
+class future {
+  public:
+    future() = default;
+    explicit future(sx_future *f) noexcept : f_(f) {}
+    ~future() {
+        if (f_) sx_future_destroy(f_);
+    }
+    future(future &&o) noexcept : f_(std::exchange(o.f_, nullptr)) {}
+    future &operator=(future &&o) noexcept {
+        std::swap(f_, o.f_);
+        return *this;
+    }
+    future(const future &) = delete;
+    future &operator=(const future &) = delete;
+
+    bool valid() const noexcept { return f_ != nullptr; }
+    void wait() const { check(sx_future_wait(f_, -1), "sx_future_wait"); }
+    bool ready() const {
+        const int st = sx_future_test(f_);
+        if (st == SX_ERR_NOT_READY) return false;
+        check(st, "sx_future_test");
+        return true;
+    }
+    float elapsed_ms() const {
+        float ms = 0;
+        check(sx_future_elapsed_ms(f_, &ms), "sx_future_elapsed_ms");
+        return ms;
+    }
+
+  private:
+    sx_future *f_ = nullptr;
+};
+
+// async_execute (Listing 2) of one of the four STREAM operations: returns once the work is
+// enqueued on the executor's target, with a future for it.
+template <class T>
+future async_execute(executor &e, sx_op op, const vector<T> &x, const vector<T> *y, vector<T> &out, double q = 0.0) {
+    sx_future *f = nullptr;
+    check(sx_execute_async(e.get(), op, x.get(), y ? y->get() : nullptr, out.get(), q, &f), "sx_execute_async");
+    return future(f);
+}
+
+// A bulk executor over a fixed shape of work items (Listing 2's bulk_async_execute): the items
+// run in one persistent launch of the batched kernel, captured once into a CUDA graph.
+class bulk_executor {
+  public:
+    bulk_executor(target &t, const sx_batch_item *items, size_t count, const sx_batch_cfg *cfg = nullptr) {
+        check(sx_batch_create(t.get(), items, count, cfg, &b_), "sx_batch_create");
+    }
+    ~bulk_executor() {
+        if (b_) sx_batch_destroy(b_);
+    }
+    bulk_executor(bulk_executor &&o) noexcept : b_(std::exchange(o.b_, nullptr)) {}
+    bulk_executor(const bulk_executor &) = delete;
+    bulk_executor &operator=(const bulk_executor &) = delete;
+
+    future bulk_async_execute() {
+        sx_future *f = nullptr;
+        check(sx_batch_launch_async(b_, &f), "sx_batch_launch_async");
+        return future(f);
+    }
+    void bulk_execute() { bulk_async_execute().wait(); }
+    sx_batch *get() const noexcept { return b_; }
+
+  private:
+    sx_batch *b_ = nullptr;
 };
 
 // A parallel policy bound to an executor: par.on(exec).
