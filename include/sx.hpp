@@ -190,13 +190,36 @@ class future {
     sx_future *f_ = nullptr;
 };
 
+// Keeps a parameter out of template argument deduction (so that y may be nullptr).
+template <class U>
+struct same_type {
+    using type = U;
+};
+
 // async_execute (Listing 2) of one of the four STREAM operations: returns once the work is
-// enqueued on the executor's target, with a future for it.
+// enqueued on the executor's target, with a future for it (y: the second input of add and
+// triad, nullptr otherwise).
 template <class T>
-future async_execute(executor &e, sx_op op, const vector<T> &x, const vector<T> *y, vector<T> &out, double q = 0.0) {
+future async_execute(executor &e, sx_op op, const vector<T> &x, const typename same_type<vector<T>>::type *y,
+                     vector<T> &out, double q = 0.0) {
     sx_future *f = nullptr;
     check(sx_execute_async(e.get(), op, x.get(), y ? y->get() : nullptr, out.get(), q, &f), "sx_execute_async");
     return future(f);
+}
+
+// execute (Listing 2): the work has completed when it returns.
+template <class T>
+void execute(executor &e, sx_op op, const vector<T> &x, const typename same_type<vector<T>>::type *y,
+             vector<T> &out, double q = 0.0) {
+    async_execute(e, op, x, y, out, q).wait();
+}
+
+// apply_execute (Listing 2): enqueued on the executor's target, no future (completion is seen
+// through a later future, executor::wait or target::synchronize).
+template <class T>
+void apply_execute(executor &e, sx_op op, const vector<T> &x, const typename same_type<vector<T>>::type *y,
+                   vector<T> &out, double q = 0.0) {
+    check(sx_execute_async(e.get(), op, x.get(), y ? y->get() : nullptr, out.get(), q, nullptr), "sx_execute_async");
 }
 
 // A bulk executor over a fixed shape of work items (Listing 2's bulk_async_execute): the items

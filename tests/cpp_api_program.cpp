@@ -61,6 +61,15 @@ int main() {
         // async_execute with a future, and bulk_async_execute over two items (Listing 2)
         const size_t m = 100003;
         sx::vector<double> x(m, 1.0, alloc), y(m, 2.0, alloc), o1(m, 0.0, alloc), o2(m, 0.0, alloc);
+        sx::apply_execute(exec, SX_OP_COPY, y, nullptr, o2);                 // o2 = 2 (no future)
+        sx::execute(exec, SX_OP_SCALE, o2, nullptr, o2, q);                  // o2 = 6, done on return
+        std::vector<double> h0(m);
+        o2.copy_to_host(h0.data());
+        for (size_t i = 0; i < m; ++i)
+            if (h0[i] != 6.0) {
+                std::fprintf(stderr, "apply_execute/execute element %zu: %.17g, want 6\n", i, h0[i]);
+                return 1;
+            }
         sx::future f = sx::async_execute(exec, SX_OP_TRIAD, x, &y, o1, q);  // o1 = 1 + 2*3
         f.wait();
         if (!f.ready() || f.elapsed_ms() < 0.0f) {
