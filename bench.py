@@ -4,8 +4,11 @@
 One step = one STREAM pass (Copy c=a, Scale b=c*q, Add c=a+b, Triad a=b+c*q; q=3) over three
 device-resident FP64 arrays of n = 2^27 elements (1 GiB each, far beyond the 126 MB L2, so no
 L2 flush is needed between steps), seeded uniform in [-1, 1).  ``value`` is the STREAM byte
-count of the pass (copy/scale 2*n*8 B, add/triad 3*n*8 B) over the device time, summed over
-ranks (weak scaling: every rank runs its own arrays; no collective on the data path).
+count of the pass (copy/scale 2*n*8 B, add/triad 3*n*8 B) over the device time, the slowest
+rank's time taken for the job: by default summed over ranks (weak scaling: every rank runs
+arrays of its own); with ``--shard`` each logical array is split into one contiguous block per
+rank (Section 4.1's block allocator and co-located executor; strong scaling) and ``value`` is
+the whole arrays' bytes over that time.  Either way there is no collective on the data path.
 
 Also reported on the same JSON line: per-kernel GB/s (FP64 and FP32), the roofline of the
 dominant kernel (Triad) against the measured HBM copy bandwidth, the end-to-end figure through
@@ -14,7 +17,9 @@ the timed region, and the sections: "batched" (the persistent batched launcher v
 per instance), "served" (the continuous-batching server vs a per-call FIFO), "small" (small
 arrays: direct launches vs CUDA graphs vs one fused kernel), "overlap" (STREAM sets on one
 stream vs one target and stream per set) and "copies" (host<->device copy bandwidth), plus the
-oracle's loops block-partitioned over the host cores.
+oracle's loops block-partitioned over the host cores.  The batched and served sections appear
+in full as "batched_detail" and "served_detail"; compact "batched" and "served" comparisons
+(graph vs per-call, continuous vs FIFO: throughput, p50/p99) close the line.
 
 ``--impl reference`` times the CPU oracle (serial C, one core) on a bounded sample instead.
 """
@@ -55,16 +60,25 @@ def _rank_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
-def job_throughput(dist, local_ms, bytes_per_rank_step, steps, world, device):
-    """Whole-job throughput (GB/s) of a weak-scaling run: every rank moved `bytes_per_rank_step`
-    per step; the job's time is the slowest rank's.  Returns (GB/s, max time in ms)."""
+def job_throughput(dist, local_ms, bytes_per_step, steps, world, device, scaling="weak"):
+    """Whole-job throughput (GB/s); the job's time is the slowest rank's (a MAX over ranks, the
+    only collective).  weak: every rank moved `bytes_per_step` per step on arrays of its own, so
+    the job moved `world` times that.  strong (the block partition): `bytes_per_step` is the
+    whole logical array's, shared out over the ranks.  Returns (GB/s, max time in ms)."""
     ms = float(local_ms)
     if dist is not None and world > 1:
         import torch
         tt = torch.tensor([ms], dtype=torch.float64, device=device)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
-    return world * bytes_per_rank_step * steps / (ms * 1e-3) / 1e9, ms
+    total = world * bytes_per_step if scaling == "weak" else bytes_per_step
+    return total * steps / (ms * 1e-3) / 1e9, ms
+
+
+def shard_block(sx, n, world, rank):
+    """(offset, count) of this rank's contiguous block of one logical n-element array (Section
+    4.1's block allocator over a vector of targets, one target per rank)."""
+    return sx.sx_block_partition(n, world, rank)
 
 
 def _measured_peaks():
@@ -199,10 +213,11 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------------
 
 def stream_kernels(sx, torch, t, stream, e, dtype_code, n, steps, warmup, seed_instance, q=Q,
-                   base_seed=None, init="uniform", doubling=False):
+                   base_seed=None, init="uniform", doubling=False, index_base=0):
     """Arrays, pass sequence and per-pass events of `steps` timed STREAM passes.  init "uniform":
     seeded values in [-1, 1); "closed-form": a = 1, b = 2, c = 0.  doubling: a is doubled once
-    after construction, as classic STREAM does before its timed loop."""
+    after construction, as classic STREAM does before its timed loop.  index_base: generator
+    index of element 0 (a block of a longer logical array)."""
     import stream_inputs as si
     base_seed = si.BASE_SEED if base_seed is None else base_seed
     es = 8 if dtype_code == sx.SX_F64 else 4
@@ -215,7 +230,7 @@ def stream_kernels(sx, torch, t, stream, e, dtype_code, n, steps, warmup, seed_i
                 sx.sx_bulk_construct(arr, v)
         else:
             for k, arr in enumerate(arrs):
-                sx.sx_seed_uniform(arr, si.array_seed(base_seed, k, seed_instance), -1.0, 1.0)
+                sx.sx_seed_uniform_at(arr, si.array_seed(base_seed, k, seed_instance), -1.0, 1.0, index_base)
         if doubling:
             sx.sx_execute_async(e[sx.SX_OP_SCALE], sx.SX_OP_SCALE, a, None, a, 2.0, future=False)
 
@@ -302,6 +317,26 @@ def batched_section(sx, torch, t, stream, args, rank):
 
     g_ms = timed(lambda: sx.sx_batch_launch(b), args.batch_reps)
     p_ms = timed(lambda: sx.sx_batch_launch_percall(b), max(3, args.batch_reps // 2))
+    # the same items through the entry point that allocates nothing (tiles of at least 1 MiB, so
+    # the workload's tiles fit its static table): device time, and the host time of each call when
+    # calls are enqueued back to back, beside that of a graph launch
+    na_cfg = dict(cfg)
+    na_cfg["chunk_bytes"] = max(cfg["chunk_bytes"], 1 << 20)
+    na_ms = timed(lambda: sx.sx_batch_run_noalloc(stream.cuda_stream, items, na_cfg), max(3, args.batch_reps // 2))
+
+    def host_us(call, reps):
+        call()
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            call()
+            out.append((time.perf_counter() - t0) * 1e6)
+        torch.cuda.synchronize()
+        return sorted(out)
+
+    na_host = host_us(lambda: sx.sx_batch_run_noalloc(stream.cuda_stream, items, na_cfg), 5)
+    g_host = host_us(lambda: sx.sx_batch_launch(b), 5)
     sx.sx_batch_set_record(b, True)
     sx.sx_batch_launch(b)
     comp_g = [v / 1e6 for v in sx.sx_batch_completion_ns(b, len(items))]
@@ -335,7 +370,12 @@ def batched_section(sx, torch, t, stream, args, rank):
     sx.sx_batch_launch_percall(b)
     sx.sx_target_synchronize(t)
     after_percall = snapshot(2)
+    poison()
+    sx.sx_batch_run_noalloc(stream.cuda_stream, items, na_cfg)
+    sx.sx_target_synchronize(t)
+    after_noalloc = snapshot(2)
     same = all(np.array_equal(g, p) for g, p in zip(after_graph, after_percall))
+    same_noalloc = all(np.array_equal(g, p) for g, p in zip(after_graph, after_noalloc))
     inputs_ok = all(np.array_equal(h, si.uniform(si.array_seed(si.BASE_SEED, 0, k), inst[k][1], np.float64)
                                    .view(np.uint64)) for k, h in zip(spot, snapshot(0)))
     sx.sx_batch_destroy(b)
@@ -353,7 +393,52 @@ def batched_section(sx, torch, t, stream, args, rank):
         "completion_ms_p99": {"graph": round(_pct(comp_g, 99), 4), "percall": round(_pct(comp_p, 99), 4)},
         "launches": {"graph": 1, "percall": len(items)},
         "graph_equals_percall_8_instances": same, "inputs_match_generator_8_instances": inputs_ok,
+        "noalloc": {"what": "sx_batch_run_noalloc on the same items, calls enqueued back to back",
+                    "cfg": na_cfg, "device_ms": round(na_ms[len(na_ms) // 2], 4),
+                    "host_us_per_call_median": round(na_host[len(na_host) // 2], 1),
+                    "graph_launch_host_us_median": round(g_host[len(g_host) // 2], 1),
+                    "equals_graph_8_instances": same_noalloc},
     }
+
+
+def batched_summary(b):
+    """The batched comparison in a few hundred bytes: one graph launch vs one launch per instance
+    (device time, STREAM bytes per second, per-instance completion p50/p99) and whether the
+    graph launch beats the per-call launches on throughput and on p99."""
+    p50, p99 = b["completion_ms_p50"], b["completion_ms_p99"]
+    return {"what": b["workload"],
+            "ms": {"graph": b["graph_ms"], "percall": b["percall_ms"]},
+            "GB/s": {"graph": b["graph_GB/s"], "percall": b["percall_GB/s"]},
+            "speedup": b["speedup"], "p50_ms": p50, "p99_ms": p99,
+            "bit_identical_8_instances": b["graph_equals_percall_8_instances"],
+            "noalloc_ms": b["noalloc"]["device_ms"],
+            "noalloc_host_us_per_call": b["noalloc"]["host_us_per_call_median"],
+            "graph_launch_host_us": b["noalloc"]["graph_launch_host_us_median"],
+            "beats_percall": {"throughput": b["graph_GB/s"] > b["percall_GB/s"],
+                              "p99": p99["graph"] < p99["percall"]}}
+
+
+def served_summary(s):
+    """The served comparison in a few hundred bytes: continuous batching vs the per-call FIFO at
+    saturation (best run and every run) and, per offered load, [continuous, fifo] p50 / p99 and
+    GB/s; and whether continuous batching beats the FIFO on saturation throughput and on p99 at
+    every load."""
+    runs = {(r["offered_load"], r["mode"]): r for r in s["runs"]}
+    loads = sorted({r["offered_load"] for r in s["runs"]})
+    per = {}
+    for ld in loads:
+        c, f = runs.get((ld, "continuous")), runs.get((ld, "fifo"))
+        if c and f:
+            per[f"{ld:g}"] = {"p50_ms": [c["p50_ms"], f["p50_ms"]], "p99_ms": [c["p99_ms"], f["p99_ms"]],
+                              "GB/s": [c["GB/s"], f["GB/s"]]}
+    sat = s["saturation_GB/s"]
+    return {"what": "continuous batching vs per-call FIFO; per load [continuous, fifo]",
+            "saturation_GB/s": sat, "saturation_runs_GB/s": s.get("saturation_runs_GB/s"),
+            "saturation_frac_measured": s.get("saturation_frac_measured"),
+            "saturation_gain": round(sat["continuous"] / sat["fifo"], 4) if sat.get("fifo") else None,
+            "loads": per,
+            "beats_fifo": {"throughput": sat["continuous"] > sat["fifo"],
+                           "p99_every_load": all(v["p99_ms"][0] <= v["p99_ms"][1] for v in per.values())}}
 
 
 def serve_run(sx, t, work, times, budget_bytes, mode, server_kw=None):
@@ -792,7 +877,11 @@ def run_ours(args):
     t = sx.target_on_torch_stream(local, stream)
     info = sx.sx_target_info_get(t)
     n = args.n
-    tune_n = args.tune_n or n  # the size whose launch shapes the pass kernels use
+    # --shard: one logical array of n elements per STREAM array, split into contiguous blocks, one
+    # per rank (strong scaling); otherwise every rank runs whole arrays of its own (weak scaling)
+    scaling = "strong" if args.shard else "weak"
+    off, n_local = shard_block(sx, n, world, rank) if args.shard else (0, n)
+    tune_n = args.tune_n or max(1, n_local)  # the size whose launch shapes the pass kernels use
     names = (("copy", sx.SX_OP_COPY), ("scale", sx.SX_OP_SCALE), ("add", sx.SX_OP_ADD),
              ("triad", sx.SX_OP_TRIAD))
     tuned = {}
@@ -827,9 +916,10 @@ def run_ours(args):
     out = {}
 
     # ---- the timed region: STREAM passes (FP64 unless --dtype f32) ---------------------------
+    instance = 0 if args.shard else rank  # blocks of one logical array share its seeds
     arrs, seq, one_pass, events, es = stream_kernels(
-        sx, torch, t, stream, execs[main_code], main_code, n, args.steps, args.warmup, rank, q,
-        args.seed, args.init, args.stream_doubling)
+        sx, torch, t, stream, execs[main_code], main_code, n_local, args.steps, args.warmup, instance, q,
+        args.seed, args.init, args.stream_doubling, index_base=off)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -849,20 +939,20 @@ def run_ours(args):
             each[name].append(ms_k)
     # sum of the passes' own device times (re-construction every 100 passes falls between them)
     total_ms = sum(events[s][0].elapsed_time(events[s][4]) for s in range(args.steps))
-    step_bytes = 10.0 * n * es
-    value, total_ms = job_throughput(dist, total_ms, step_bytes, args.steps, world, "cuda")
+    step_bytes = 10.0 * n * es  # the whole logical arrays (shard) or one rank's arrays (weak)
+    value, total_ms = job_throughput(dist, total_ms, step_bytes, args.steps, world, "cuda", scaling)
     bytes_per = {"copy": 2, "scale": 2, "add": 3, "triad": 3}
     kernels = {}
     for name in per:
         ms = per[name] / args.steps
-        gbs = bytes_per[name] * n * es / (ms * 1e-3) / 1e9
+        gbs = bytes_per[name] * n_local * es / (ms * 1e-3) / 1e9
         # STREAM's own convention besides the mean: the best pass, excluding the first
         rest = each[name][1:] or each[name]
         kernels[name] = {"ms": round(ms, 5), "GB/s": round(gbs, 1),
                          "frac_measured": round(gbs / peak, 4),
                          "frac_nominal_8TBs": round(gbs / NOMINAL_HBM_GBS, 4),
                          "ms_min_avg_max": [round(min(rest), 5), round(sum(rest) / len(rest), 5), round(max(rest), 5)],
-                         "GB/s_best": round(bytes_per[name] * n * es / (min(rest) * 1e-3) / 1e9, 1)}
+                         "GB/s_best": round(bytes_per[name] * n_local * es / (min(rest) * 1e-3) / 1e9, 1)}
     clk = clocks.summary()
 
     # ---- FP32 per-kernel figures (same shape, fewer steps) -----------------------------------
@@ -872,15 +962,15 @@ def run_ours(args):
             sx.sx_free(arr)
         steps32 = max(3, min(args.steps, 200))
         arrs, seq, one_pass, ev32, es32 = stream_kernels(
-            sx, torch, t, stream, execs[sx.SX_F32], sx.SX_F32, n, steps32, args.warmup, rank, q,
-            args.seed, args.init, args.stream_doubling)
+            sx, torch, t, stream, execs[sx.SX_F32], sx.SX_F32, n_local, steps32, args.warmup, instance, q,
+            args.seed, args.init, args.stream_doubling, index_base=off)
         for s in range(steps32):
             one_pass(ev32[s])
         torch.cuda.synchronize()
         kernels_f32 = {}
         for k, (name, *_r) in enumerate(seq):
             ms = sum(ev32[s][k].elapsed_time(ev32[s][k + 1]) for s in range(steps32)) / steps32
-            gbs = bytes_per[name] * n * es32 / (ms * 1e-3) / 1e9
+            gbs = bytes_per[name] * n_local * es32 / (ms * 1e-3) / 1e9
             kernels_f32[name] = {"ms": round(ms, 5), "GB/s": round(gbs, 1),
                                  "frac_measured": round(gbs / peak, 4)}
     for arr in arrs:
@@ -893,11 +983,11 @@ def run_ours(args):
         host = []
         tdt, ndt = (torch.float32, np.float32) if main_code == sx.SX_F32 else (torch.float64, np.float64)
         for k in range(3):
-            h = torch.empty(n, dtype=tdt, pin_memory=True)
-            h.numpy()[:] = si.uniform(si.array_seed(si.BASE_SEED if args.seed is None else args.seed, k, rank),
-                                      n, ndt) if k == 0 else 0.0
+            h = torch.empty(n_local, dtype=tdt, pin_memory=True)
+            h.numpy()[:] = si.uniform(si.array_seed(si.BASE_SEED if args.seed is None else args.seed, k, instance),
+                                      n_local, ndt, start=off) if k == 0 else 0.0
             host.append(h)
-        dev = [sx.sx_alloc(t, main_code, n) for _ in range(3)]
+        dev = [sx.sx_alloc(t, main_code, n_local) for _ in range(3)]
         esync = sx.sx_executor_create(t, sx.SX_PAR, forced.get(args.variant))
         sx.sx_stream_host(esync, *(h.data_ptr() for h in host), *dev, q, 1)  # warm
         if dist:
@@ -906,9 +996,9 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             sx.sx_stream_host(esync, *(h.data_ptr() for h in host), *dev, q, 1)
         el = time.perf_counter() - t0
-        e2e_gbs, el_ms = job_throughput(dist, el * 1e3, step_bytes, args.e2e_steps, world, "cuda")
+        e2e_gbs, el_ms = job_throughput(dist, el * 1e3, step_bytes, args.e2e_steps, world, "cuda", scaling)
         e2e = {"value": round(e2e_gbs, 2), "unit": "GB/s",
-               "h2d_bytes_per_step": 3 * n * es, "d2h_bytes_per_step": 3 * n * es,
+               "h2d_bytes_per_step": 3 * n_local * es, "d2h_bytes_per_step": 3 * n_local * es,
                "steps": args.e2e_steps,
                "what": "sx_stream_host: h2d a,b,c + one pass + d2h a,b,c from pinned host memory, "
                        "pipelined in 32 MiB chunks over 3 streams; host clock"}
@@ -948,24 +1038,24 @@ def run_ours(args):
                           f"{el:.1f} s, one contiguous block per pinned thread", "cpu": _cpu_model()}
 
     triad_ms = per["triad"] / args.steps
-    achieved = 3 * n * es / (triad_ms * 1e-3) / 1e9
+    achieved = 3 * n_local * es / (triad_ms * 1e-3) / 1e9
     traffic = None
     # the captured traffic holds for the captured case only: FP64, q = 3, this n and launch shape
     same_kernel = main_code == sx.SX_F64 and q == Q and \
         all(tuned["f64"]["triad"].get(k) == v for k, v in NCU_TRAFFIC["cfg"].items())
     if NCU_TRAFFIC["bytes"] and NCU_TRAFFIC["source_sha256"] == _kernel_source_sha() \
-            and NCU_TRAFFIC["n"] == n and same_kernel:
+            and NCU_TRAFFIC["n"] == n_local and same_kernel:
         traffic = NCU_TRAFFIC["bytes"]
     roofline = {"bound": "hbm", "kernel": f"triad {main_name}", "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "frac_nominal_8TBs": round(achieved / NOMINAL_HBM_GBS, 4),
-                "algorithmic_bytes_per_launch": 3 * n * es, "traffic": traffic}
+                "algorithmic_bytes_per_launch": 3 * n_local * es, "traffic": traffic}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": main_name,
+            "higher_is_better": True, "scaling": scaling, "vs_baseline": None, "dtype": main_name,
             "data": ("synthetic: a=1, b=2, c=0" if args.init == "closed-form" else
                      "synthetic: seeded SplitMix64 uniform [-1,1)") + ", constructed on the device" +
                     (", a doubled once" if args.stream_doubling else ""),
@@ -973,8 +1063,11 @@ def run_ours(args):
                                    f"({n * es / 2 ** 30:g} GiB each), q={q:g}; step = one pass "
                                    "copy,scale,add,triad (4 launches)",
                        "n": n, "device": info["name"], "sm_count": info["sm_count"],
-                       "l2": ("inputs larger than L2: no flush" if 3 * n * es > info["l2_bytes"] else
+                       "l2": ("inputs larger than L2: no flush" if 3 * n_local * es > info["l2_bytes"] else
                               "inputs fit in L2 (L2-resident regime)"),
+                       "parallelism": (f"block partition of each array over {world} rank(s); rank 0 holds "
+                                       f"[{off}, {off + n_local})" if args.shard else
+                                       f"{world} replica(s), arrays of their own"),
                        "variant": args.variant, "init": args.init, "stream_doubling": args.stream_doubling,
                        "launch": tuned, "autotuned": bool(args.tune)},
             "kernels": kernels, "kernels_f32": kernels_f32, "roofline": roofline,
@@ -982,7 +1075,17 @@ def run_ours(args):
             "gpu_launches": 4 * args.steps + (3 + int(args.stream_doubling)) * ((args.steps - 1) // RESEED_EVERY),
             "clocks": clk,
         }
-        line.update(extra)
+        # the verbose sections first; the compact batched and served comparisons close the line,
+        # so that a reader of its last few kilobytes still sees them
+        for k, v in extra.items():
+            if k in ("batched", "served"):
+                line[k + "_detail"] = v
+            else:
+                line[k] = v
+        if "batched" in extra:
+            line["batched"] = batched_summary(extra["batched"])
+        if "served" in extra:
+            line["served"] = served_summary(extra["served"])
         print(json.dumps(line), flush=True)
     for d in execs.values():
         for ex in d.values():
@@ -997,6 +1100,9 @@ def run_ours(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--shard", action="store_true",
+                    help="split each logical n-element array into one contiguous block per rank "
+                         "(Section 4.1's block allocator; strong scaling) instead of one replica per rank")
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")

@@ -196,12 +196,29 @@ int sx_bulk_construct(sx_array *a, double value);
  * of SplitMix64 (Steele, Lea & Flood 2014; Vigna's 64-bit finaliser) started from state
  * `seed`.  Enqueued on the target stream. */
 int sx_seed_uniform(sx_array *a, uint64_t seed, double lo, double hi);
+/* sx_seed_uniform with the generator indices shifted: element i takes the value that element
+ * (index_base + i) of sx_seed_uniform's array from the same seed would take.  So an array that
+ * holds elements [off, off + n) of a longer logical array (one block of sx_block_partition)
+ * is constructed with index_base = off and equals that slice of the whole.  SX_ERR_INVALID if
+ * index_base + n - 1 overflows 64 bits.  Enqueued on the target stream. */
+int sx_seed_uniform_at(sx_array *a, uint64_t seed, double lo, double hi, uint64_t index_base);
 /* bulk_destroy (Section 3.2, Listing 1: ends the lifetime of the array's elements on its
  * target, never fails for a valid array).  The element types here are trivially destructible,
  * so nothing runs on the device and no memory is freed (sx_free does that); the call exists so
  * that code written against the allocator interface pairs each bulk construction with its
  * destruction.  SX_ERR_INVALID only for a NULL array. */
 int sx_bulk_destroy(sx_array *a);
+
+/* ---- block partition of one logical array over several targets: Section 4.1 (the block
+ *      allocator divides the bytes evenly over a vector of targets; the executor runs each
+ *      block's work on the target that holds it) ------------------------------------------- */
+/* The block of part `part` (0..parts-1) when n elements are divided over `parts` targets in
+ * contiguous blocks of ceil(n / parts) elements: *offset = min(n, part * ceil(n / parts)),
+ * *count = min(n, *offset + ceil(n / parts)) - *offset.  The blocks of parts 0..parts-1 tile
+ * [0, n) exactly, in order; trailing parts may be empty when parts does not divide n.  Host
+ * arithmetic only.  SX_ERR_INVALID for parts < 1, part outside [0, parts), n >= 2^63 or a NULL
+ * output. */
+int sx_block_partition(uint64_t n, int parts, int part, uint64_t *offset, uint64_t *count);
 
 /* ---- host<->device copy: Section 4.2 (copy specialised to CUDA memcpy) ---------------- */
 /* Copy n elements between host memory and the array, starting at element 0.  The blocking
@@ -353,12 +370,17 @@ int sx_batch_destroy(sx_batch *b);
  *            cfg->chunk_bytes, else SX_ERR_INVALID before anything is launched
  *   cfg      launch shape as sx_batch_cfg (NULL or zero fields = 256 KiB tiles, 512 threads,
  *            4 blocks per SM, 32-byte vectors; the autotuner's table is not consulted)
- * Returns once the work is enqueued.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress), so make that first call before any stream capture.  All
- * calls share the one array and each overwrites the tables it uses: calls whose work overlaps
- * on the GPU (different streams, no ordering between them) race and give wrong results;
- * calls on one stream, or otherwise ordered, are safe.  Calls from several host threads take
- * turns on a lock. */
+ * Returns once the work is enqueued.  The tables are copied to the device from static pageable
+ * host staging, which the driver stages before the copy call returns: the call may therefore
+ * block the host until the stream's earlier work has drained, and the staging may be refilled
+ * by the next call at once.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress).  While `stream` is being captured into a CUDA graph the call is
+ * refused with SX_ERR_STATE before anything is enqueued: a captured copy would read the host
+ * staging at every replay, after later calls had put their own items there.  All calls share
+ * the one array and each overwrites the tables it uses: calls whose work overlaps on the GPU
+ * (different streams, no ordering between them) race and give wrong results; calls on one
+ * stream, or otherwise ordered, are safe, with no synchronization between them.  Calls from
+ * several host threads take turns on a lock. */
 #define SX_NOALLOC_MAX_ITEMS 4096
 #define SX_NOALLOC_MAX_TILES 65536
 #define SX_NOALLOC_SCRATCH_BYTES 950272 /* 4096 items x 104 B + 65536 tiles x 8 B */

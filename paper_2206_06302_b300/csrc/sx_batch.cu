@@ -905,6 +905,18 @@ extern "C" int sx_batch_run_noalloc(void *stream, const sx_batch_item *items, si
     if (want > kNoAllocMaxTiles)
         return fail(SX_ERR_INVALID, "the batch needs %zu work tiles but the static scratch holds %zu; "
                     "raise chunk_bytes or split the batch", want, kNoAllocMaxTiles);
+    cudaStream_t s = (cudaStream_t)stream;
+    // The table copies below read the static host staging when they execute.  Captured into a
+    // graph, they would read it at every replay, after later calls had refilled it with their
+    // own items (whose arrays may since have been freed), so a capturing stream is refused.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce == cudaErrorStreamCaptureImplicit || (ce == cudaSuccess && cap != cudaStreamCaptureStatusNone)) {
+        cudaGetLastError();
+        return fail(SX_ERR_STATE, "the stream is being captured into a CUDA graph; this call copies its "
+                    "tables from host staging that the next call overwrites, so it cannot be captured");
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamIsCapturing");
     int dev = 0;
     SX_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SX_ERR_INVALID, "device %d out of range", dev);
@@ -915,11 +927,12 @@ extern "C" int sx_batch_run_noalloc(void *stream, const sx_batch_item *items, si
     SX_TRY(fill_tables(items, count, c.chunk_bytes, g_noalloc_host_items, g_noalloc_host_tiles,
                        kNoAllocMaxTiles, &nt, nullptr));
     if (nt == 0) return SX_OK;
-    cudaStream_t s = (cudaStream_t)stream;
     char *base = static_cast<char *>(g_noalloc_dev_ptr[dev]);
     DevItem *d_items = reinterpret_cast<DevItem *>(base);
     DevTile *d_tiles = reinterpret_cast<DevTile *>(base + kNoAllocItemBytes);
     // copies from pageable host memory: the staging arrays may be refilled once these return
+    // (the driver stages pageable data before returning, and may wait for the stream's earlier
+    // work to do so)
     SX_CUDA(cudaMemcpyAsync(d_items, g_noalloc_host_items, count * sizeof(DevItem), cudaMemcpyHostToDevice, s));
     SX_CUDA(cudaMemcpyAsync(d_tiles, g_noalloc_host_tiles, nt * sizeof(DevTile), cudaMemcpyHostToDevice, s));
     uint64_t grid = (uint64_t)g_noalloc_dev_sms[dev] * c.blocks_per_sm;

@@ -386,6 +386,28 @@ int sx_seed_uniform(sx_array *a, uint64_t seed, double lo, double hi) {
     return launch_seed(a->t->stream, a->dtype, a->ptr, a->n, seed, lo, hi, 0);
 }
 
+int sx_seed_uniform_at(sx_array *a, uint64_t seed, double lo, double hi, uint64_t index_base) {
+    if (!a) return fail(SX_ERR_INVALID, "array is NULL");
+    if (a->n && index_base > UINT64_MAX - (a->n - 1))
+        return fail(SX_ERR_INVALID, "index_base + n - 1 exceeds the generator's 64-bit index");
+    DeviceScope ds(a->t->device);
+    return launch_seed(a->t->stream, a->dtype, a->ptr, a->n, seed, lo, hi, index_base);
+}
+
+// ---- block partition of one logical array over several targets (Section 4.1) ----------------
+int sx_block_partition(uint64_t n, int parts, int part, uint64_t *offset, uint64_t *count) {
+    if (!offset || !count) return fail(SX_ERR_INVALID, "NULL argument");
+    if (parts < 1) return fail(SX_ERR_INVALID, "parts=%d: need at least 1", parts);
+    if (part < 0 || part >= parts) return fail(SX_ERR_INVALID, "part=%d out of [0, %d)", part, parts);
+    if (n > (UINT64_MAX >> 1)) return fail(SX_ERR_INVALID, "n too large");
+    const uint64_t block = n / (uint64_t)parts + (n % (uint64_t)parts != 0);  // ceil(n / parts)
+    const uint64_t lo = std::min<uint64_t>(n, (uint64_t)part * block);
+    const uint64_t hi = std::min<uint64_t>(n, lo + block);
+    *offset = lo;
+    *count = hi - lo;
+    return SX_OK;
+}
+
 // ---- host <-> device copies (Section 4.2) ------------------------------------------------------
 static int copy_common(sx_array *dev, const void *host, size_t n, bool h2d, bool async) {
     if (!dev || (!host && n)) return fail(SX_ERR_INVALID, "NULL argument");

@@ -126,6 +126,8 @@ _PROTOS = {
     "sx_bulk_construct": [P, D],
     "sx_bulk_destroy": [P],
     "sx_seed_uniform": [P, U64, D, D],
+    "sx_seed_uniform_at": [P, U64, D, D, U64],
+    "sx_block_partition": [U64, I, I, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
     "sx_copy_h2d": [P, P, SZ],
     "sx_copy_d2h": [P, P, SZ],
     "sx_copy_h2d_async": [P, P, SZ],
@@ -308,6 +310,17 @@ def sx_bulk_destroy(a) -> None:
 
 def sx_seed_uniform(a, seed: int, lo: float = -1.0, hi: float = 1.0) -> None:
     _check(lib.sx_seed_uniform(a, seed, lo, hi), "sx_seed_uniform")
+
+
+def sx_seed_uniform_at(a, seed: int, lo: float = -1.0, hi: float = 1.0, index_base: int = 0) -> None:
+    _check(lib.sx_seed_uniform_at(a, seed, lo, hi, index_base), "sx_seed_uniform_at")
+
+
+def sx_block_partition(n: int, parts: int, part: int) -> tuple[int, int]:
+    """(offset, count) of block `part` of n elements divided over `parts` targets."""
+    off, cnt = C.c_uint64(), C.c_uint64()
+    _check(lib.sx_block_partition(n, parts, part, C.byref(off), C.byref(cnt)), "sx_block_partition")
+    return off.value, cnt.value
 
 
 def sx_copy_h2d(a, host_ptr: int, n: int) -> None:

@@ -863,3 +863,51 @@ def test_cpp_layer_closed_form(tmp_path):
     from test_abi import build_cpp_client
     r = subprocess.run([build_cpp_client(tmp_path)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "closed form ok" in r.stdout, (r.returncode, r.stdout, r.stderr)
+
+
+@pytest.mark.parametrize("n", [1 << 16, 1 << 20])
+def test_per_op_autotuner_search(tmp_path, n):
+    """sx_tune searches the launch shapes of the three families for each of the four kernels and
+    both types: the shape it returns is valid (an executor fixed to it resolves to it unchanged),
+    it is stored under (device, op, type, log2 n) and found again by sx_tune_lookup, an AUTO
+    executor launches with it, the results under it equal the oracle's bit for bit (with a
+    ragged tail: n + 37 is in the same log2 bucket), and the table round-trips through
+    sx_tune_save / sx_tune_load."""
+    t = sx.sx_target_create(0)
+    sx.sx_tune_clear()
+    found = {}
+    try:
+        for dt, code in ((np.float64, sx.SX_F64), (np.float32, sx.SX_F32)):
+            for name, op in OPS.items():
+                best, gbs = sx.sx_tune(t, op, code, n)
+                assert gbs > 0 and best["variant"] in (sx.SX_VARIANT_VECTOR, sx.SX_VARIANT_BULK,
+                                                       sx.SX_VARIANT_TMA), best
+                fixed = sx.sx_executor_create(t, sx.SX_PAR, best)  # refused if the shape were invalid
+                assert sx.sx_executor_resolve(fixed, op, code, n) == best
+                sx.sx_executor_destroy(fixed)
+                assert sx.sx_tune_lookup(t, op, code, n) == best
+                assert sx.sx_tune_lookup(t, op, code, n + 37) == best
+                e = sx.sx_executor_create(t, sx.SX_PAR)
+                try:
+                    assert sx.sx_executor_resolve(e, op, code, n + 37) == best
+                    x, y = _inputs(n + 37, dt, 29)
+                    dx, dy, do = to_device(t, x), to_device(t, y), empty(t, dt, x.size)
+                    sx.sx_execute(e, op, dx, dy, do, 3.0)
+                    assert_bitwise(to_host(do), oracle.apply(name, x, y, 3.0), f"tuned {name} {dt.__name__} n={n}")
+                    assert sx.sx_array_guard_ok(do)
+                    for h in (dx, dy, do):
+                        sx.sx_free(h)
+                finally:
+                    sx.sx_executor_destroy(e)
+                found[(op, code)] = best
+        path = str(tmp_path / "tuned.json")
+        sx.sx_tune_save(path)
+        sx.sx_tune_clear()
+        assert sx.sx_tune_lookup(t, sx.SX_OP_TRIAD, sx.SX_F64, n) is None
+        sx.sx_tune_load(path)
+        for (op, code), best in found.items():
+            assert sx.sx_tune_lookup(t, op, code, n) == best
+    finally:
+        sx.sx_tune_clear()
+        sx.load_shipped_tune_table()
+        sx.sx_target_destroy(t)
