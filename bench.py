@@ -212,12 +212,14 @@ def run_reference(args):
 # GPU legs
 # ----------------------------------------------------------------------------------------------
 
-def stream_kernels(sx, torch, t, stream, e, dtype_code, n, steps, warmup, seed_instance, q=Q,
+def stream_kernels(sx, torch, t, stream, e, dtype_code, n, steps, seed_instance, q=Q,
                    base_seed=None, init="uniform", doubling=False, index_base=0):
-    """Arrays, pass sequence and per-pass events of `steps` timed STREAM passes.  init "uniform":
-    seeded values in [-1, 1); "closed-form": a = 1, b = 2, c = 0.  doubling: a is doubled once
-    after construction, as classic STREAM does before its timed loop.  index_base: generator
-    index of element 0 (a block of a longer logical array)."""
+    """Arrays (constructed), pass sequence, a pass function and per-pass events of `steps` timed
+    STREAM passes.  The caller runs its warm-up passes with the same function right before the
+    timed ones, so that the timed region does not start on a GPU left idle by construction and
+    set-up.  init "uniform": seeded values in [-1, 1); "closed-form": a = 1, b = 2, c = 0.
+    doubling: a is doubled once after construction, as classic STREAM does before its timed
+    loop.  index_base: generator index of element 0 (a block of a longer logical array)."""
     import stream_inputs as si
     base_seed = si.BASE_SEED if base_seed is None else base_seed
     es = 8 if dtype_code == sx.SX_F64 else 4
@@ -241,8 +243,8 @@ def stream_kernels(sx, torch, t, stream, e, dtype_code, n, steps, warmup, seed_i
 
     def one_pass(evs=None):
         # The workload is 100 passes from seeded inputs (|a| grows as 15^k: FP64 would reach
-        # inf near k = 262).  Every 100 passes the arrays are constructed again, between the
-        # per-pass events, so it is not in the timed sum.
+        # inf near k = 262).  Every 100 passes (warm-up passes included) the arrays are
+        # constructed again, between the per-pass events, so it is not in the timed sum.
         if count[0] and count[0] % RESEED_EVERY == 0:
             construct()
         count[0] += 1
@@ -253,13 +255,15 @@ def stream_kernels(sx, torch, t, stream, e, dtype_code, n, steps, warmup, seed_i
             if evs is not None:
                 evs[k + 1].record(stream)
 
-    for _ in range(warmup):
-        one_pass()
-    count[0] = 0
-    construct()
     torch.cuda.synchronize()
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
     return arrs, seq, one_pass, events, es
+
+
+def reseeds_between(first, count):
+    """Constructions that passes number first .. first + count - 1 (from 0) start with: one
+    before every pass whose number is a positive multiple of RESEED_EVERY."""
+    return sum(1 for c in range(first, first + count) if c and c % RESEED_EVERY == 0)
 
 
 def _pct(xs, p):
@@ -918,12 +922,14 @@ def run_ours(args):
     # ---- the timed region: STREAM passes (FP64 unless --dtype f32) ---------------------------
     instance = 0 if args.shard else rank  # blocks of one logical array share its seeds
     arrs, seq, one_pass, events, es = stream_kernels(
-        sx, torch, t, stream, execs[main_code], main_code, n_local, args.steps, args.warmup, instance, q,
+        sx, torch, t, stream, execs[main_code], main_code, n_local, args.steps, instance, q,
         args.seed, args.init, args.stream_doubling, index_base=off)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
+        for _ in range(args.warmup):
+            one_pass()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         for s in range(args.steps):
             one_pass(events[s])
         torch.cuda.synchronize()
@@ -962,8 +968,10 @@ def run_ours(args):
             sx.sx_free(arr)
         steps32 = max(3, min(args.steps, 200))
         arrs, seq, one_pass, ev32, es32 = stream_kernels(
-            sx, torch, t, stream, execs[sx.SX_F32], sx.SX_F32, n_local, steps32, args.warmup, instance, q,
+            sx, torch, t, stream, execs[sx.SX_F32], sx.SX_F32, n_local, steps32, instance, q,
             args.seed, args.init, args.stream_doubling, index_base=off)
+        for _ in range(args.warmup):
+            one_pass()
         for s in range(steps32):
             one_pass(ev32[s])
         torch.cuda.synchronize()
@@ -1072,7 +1080,7 @@ def run_ours(args):
                        "launch": tuned, "autotuned": bool(args.tune)},
             "kernels": kernels, "kernels_f32": kernels_f32, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 4 * args.steps + (3 + int(args.stream_doubling)) * ((args.steps - 1) // RESEED_EVERY),
+            "gpu_launches": 4 * args.steps + (3 + int(args.stream_doubling)) * reseeds_between(args.warmup, args.steps),
             "clocks": clk,
         }
         # the verbose sections first; the compact batched and served comparisons close the line,

@@ -410,15 +410,16 @@ int sx_tune_clear(void);
 typedef struct sx_server sx_server;
 
 /* Modes.  CONTINUOUS: the server thread runs "steps"; each step is one launch of the batched
- * kernel holding a piece of every active request's current phase (inputs construction, then the
- * operation), the step's byte budget shared out so that short requests finish in one step and
- * long ones share the rest.  A request whose whole work is at most a quarter of the budget, taken
- * whole by a step, runs as one piece that constructs its inputs and then applies the operation
- * tile by tile, and is DONE as soon as that piece's last tile has finished (the device sets a
- * completion word), before the rest of the step.  Requests that arrive while steps are on the
- * GPU are admitted as slots and arena memory free up and join the next step.  FIFO: the
- * per-call baseline; each admitted request is enqueued at once as its own launches (construct x,
- * construct y, op) on the stream, in arrival order. */
+ * kernel holding a piece (a range of elements) of every scheduled request, the step's byte budget
+ * shared out so that short requests finish in one step and long ones share the rest.  A piece
+ * constructs its range of the inputs and then applies the operation to it, tile by tile (unless
+ * split_phases: then requests over a quarter of the budget construct their inputs in one phase
+ * and run the operation in a later one).  A request that a step takes whole, in one piece, is
+ * DONE as soon as that piece's last tile has finished (the device sets a completion word),
+ * before the rest of the step.  Requests that arrive while steps are on the GPU are admitted as
+ * slots and arena memory free up and join the next step.  FIFO: the per-call baseline; each
+ * admitted request is enqueued at once as its own launches (construct x, construct y, op) on the
+ * stream, in arrival order. */
 enum { SX_SERVE_CONTINUOUS = 0, SX_SERVE_FIFO = 1 };
 typedef struct sx_server_cfg {
     uint64_t budget_bytes;   /* device arena the server allocates once; admission bound.  Large
@@ -428,12 +429,16 @@ typedef struct sx_server_cfg {
     int32_t max_active;      /* requests admitted at once (slots), 1..65536; 0 = 256          */
     int32_t chunk_bytes;     /* CONTINUOUS: byte budget of one step (1 MiB..2 GiB); 0 = 1 GiB   */
     int32_t steps_in_flight; /* CONTINUOUS: launched steps not yet completed (1..8); 0 = 2    */
-    int32_t threads, blocks_per_sm, vec_bytes;  /* batched-kernel shape; 0 = default        */
-    int32_t tile_bytes;      /* CONTINUOUS: work-tile bytes of the batched kernel; 0 = 256 KiB */
+    int32_t threads, blocks_per_sm, vec_bytes;  /* batched-kernel shape; 0 = 256, 4, 32     */
+    int32_t tile_bytes;      /* CONTINUOUS: work-tile bytes of the batched kernel; 0 = 128 KiB */
     int32_t policy;          /* CONTINUOUS: how a step's budget is shared, SX_SERVE_POLICY_*  */
     int32_t serialize_steps; /* CONTINUOUS: 0 = a step may start while the previous one ends
                                 (programmatic dependent launch; pieces that need the previous
                                 step's data wait for it); 1 = steps run strictly one after another */
+    int32_t split_phases;    /* CONTINUOUS: 0 = every piece constructs its range of the inputs and
+                                then applies the operation to it, tile by tile (the inputs are read
+                                back from L2); 1 = requests over a quarter of the step budget run
+                                in two phases, inputs first, the operation in a later piece       */
 } sx_server_cfg;
 
 /* CONTINUOUS sharing policies.  SRPT (default): shortest remaining work first; each request in
@@ -483,7 +488,7 @@ typedef struct sx_server_stats {
     double host_step_seconds;  /* CONTINUOUS: host time spent building and launching steps */
     double host_admit_seconds; /* host time spent in admission passes                      */
     uint64_t cancelled;        /* requests cancelled (sx_server_cancel)                     */
-    uint64_t fused;            /* CONTINUOUS: short requests run as one construct-then-operate
+    uint64_t fused;            /* CONTINUOUS: requests run whole as one construct-then-operate
                                   piece                                                     */
     uint64_t early_done;       /* CONTINUOUS: of those, DONE from the piece's own completion
                                   word, before the step holding it had completed            */

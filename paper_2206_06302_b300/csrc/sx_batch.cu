@@ -53,10 +53,8 @@ struct DevTile {
     uint32_t index;  // tile index within the item
 };
 
-// coherent: the inputs were written earlier in the same kernel, so the body reads them with
-// coherent loads instead of the read-only path.
 template <int OP, class T, int VB, int MM>
-__device__ __forceinline__ void tile_vector(const DevItem &it, uint64_t start, uint64_t cnt, bool coherent) {
+__device__ __forceinline__ void tile_vector(const DevItem &it, uint64_t start, uint64_t cnt) {
     constexpr int W = VB / 8;
     constexpr int EPV = VB / (int)sizeof(T);
     constexpr bool HY = has_y<OP>();
@@ -92,16 +90,12 @@ __device__ __forceinline__ void tile_vector(const DevItem &it, uint64_t start, u
         uint64_t xa[W], ya[W], xc[W], yc[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) ya[k] = yc[k] = 0;
-        auto load = [coherent](const char *a, uint64_t(&w)[W]) {
-            if (coherent) ldv<VB, 2>(a, w);
-            else ldv<VB, 0>(a, w);
-        };
-        load(xb + v * VB, xa);
-        if constexpr (HY) load(yb + v * VB, ya);
+        ldv<VB, 0>(xb + v * VB, xa);
+        if constexpr (HY) ldv<VB, 0>(yb + v * VB, ya);
         const bool two = PER == 2 && v2 < nvec;
         if (two) {
-            load(xb + v2 * VB, xc);
-            if constexpr (HY) load(yb + v2 * VB, yc);
+            ldv<VB, 0>(xb + v2 * VB, xc);
+            if constexpr (HY) ldv<VB, 0>(yb + v2 * VB, yc);
         }
         uint64_t r[W];
 #pragma unroll
@@ -125,28 +119,28 @@ __device__ __forceinline__ void tile_seed(const DevItem &it, uint64_t start, uin
 }
 
 template <int VB>
-__device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint64_t cnt, bool coherent = false) {
+__device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint64_t cnt) {
     const bool f64 = it.dtype == SX_F64;
     switch (it.op) {
         case SX_OP_COPY:
-            if (f64) tile_vector<SX_OP_COPY, double, VB, 0>(it, start, cnt, coherent);
-            else tile_vector<SX_OP_COPY, float, VB, 0>(it, start, cnt, coherent);
+            if (f64) tile_vector<SX_OP_COPY, double, VB, 0>(it, start, cnt);
+            else tile_vector<SX_OP_COPY, float, VB, 0>(it, start, cnt);
             break;
         case SX_OP_SCALE:
-            if (!f64) tile_vector<SX_OP_SCALE, float, VB, 0>(it, start, cnt, coherent);
-            else if (it.mulv == 4) tile_vector<SX_OP_SCALE, double, VB, 4>(it, start, cnt, coherent);
-            else if (it.mulv == 2) tile_vector<SX_OP_SCALE, double, VB, 2>(it, start, cnt, coherent);
-            else tile_vector<SX_OP_SCALE, double, VB, 0>(it, start, cnt, coherent);
+            if (!f64) tile_vector<SX_OP_SCALE, float, VB, 0>(it, start, cnt);
+            else if (it.mulv == 4) tile_vector<SX_OP_SCALE, double, VB, 4>(it, start, cnt);
+            else if (it.mulv == 2) tile_vector<SX_OP_SCALE, double, VB, 2>(it, start, cnt);
+            else tile_vector<SX_OP_SCALE, double, VB, 0>(it, start, cnt);
             break;
         case SX_OP_ADD:
-            if (f64) tile_vector<SX_OP_ADD, double, VB, 0>(it, start, cnt, coherent);
-            else tile_vector<SX_OP_ADD, float, VB, 0>(it, start, cnt, coherent);
+            if (f64) tile_vector<SX_OP_ADD, double, VB, 0>(it, start, cnt);
+            else tile_vector<SX_OP_ADD, float, VB, 0>(it, start, cnt);
             break;
         case SX_OP_TRIAD:
-            if (!f64) tile_vector<SX_OP_TRIAD, float, VB, 0>(it, start, cnt, coherent);
-            else if (it.mulv == 4) tile_vector<SX_OP_TRIAD, double, VB, 4>(it, start, cnt, coherent);
-            else if (it.mulv == 2) tile_vector<SX_OP_TRIAD, double, VB, 2>(it, start, cnt, coherent);
-            else tile_vector<SX_OP_TRIAD, double, VB, 0>(it, start, cnt, coherent);
+            if (!f64) tile_vector<SX_OP_TRIAD, float, VB, 0>(it, start, cnt);
+            else if (it.mulv == 4) tile_vector<SX_OP_TRIAD, double, VB, 4>(it, start, cnt);
+            else if (it.mulv == 2) tile_vector<SX_OP_TRIAD, double, VB, 2>(it, start, cnt);
+            else tile_vector<SX_OP_TRIAD, double, VB, 0>(it, start, cnt);
             break;
         case SX_OP_SEED:
             if (f64 && it.q == -1.0 && it.q2 == 1.0) tile_seed<double, true>(it, start, cnt);
@@ -157,35 +151,105 @@ __device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint
     }
 }
 
-// Construct-then-operate piece of a serving step (a whole short request): each tile's block
-// constructs the tile's x (and y) from their seeds exactly as a SEED item does, waits for its own
-// stores, then applies the operation to them, read back from memory with coherent loads.
+// Construct-then-operate piece of a serving step: each element's inputs are drawn from their
+// seeds in registers and stored, and the operation is applied to those register values and
+// stored.  The result has the bits of constructing the inputs and then running the operation
+// over memory (the operation would read back exactly the values stored), without reading the
+// inputs back and without a barrier between the two: the tile's DRAM traffic is its stores.
+//
+// Binary64 inputs on [-1, 1): kFusedPm1Sub of every four elements take the FP64-subtraction
+// form of the value and the others the integer-unit assembly (the same bits either way).  The
+// operation's additions (and half of its products) already occupy the FP64 pipe, so fewer of
+// these pieces' values go there than in plain construction (5 of 8): on the served workload 0 or
+// 1 of 4 moved 8.5-8.8 TB/s, 2 of 4 8.2-8.8, 3 of 4 7.7-8.1, 4 of 4 7.2-7.5.
+#ifndef SX_FUSED_PM1_SUB
+#define SX_FUSED_PM1_SUB 1
+#endif
+constexpr int kFusedPm1Sub = SX_FUSED_PM1_SUB;
+
 template <class T, bool PM1>
-__device__ __forceinline__ void tile_construct(const DevItem &it, void *arr, uint64_t seed, uint64_t start,
-                                               uint64_t cnt) {
-    const T lo = (T)it.q2;
-    const T span = (T)it.q3 - lo;  // RN(hi - lo) in T, as the host-side generator defines it
-    seed_range<T, PM1>(static_cast<T *>(arr) + start, cnt, seed, it.index_base + start, lo, span, threadIdx.x,
-                       blockDim.x);
+__device__ __forceinline__ T fused_input(uint64_t z, T lo, T span, int j) {
+    if constexpr (sizeof(T) == 4) {
+        return seeded_value(splitmix_mix<true>(z), (float)lo, (float)span);  // uses bits 40..63 only
+    } else if constexpr (PM1) {
+        const uint64_t w = splitmix_mix(z);
+        return (j & 3) < kFusedPm1Sub ? seeded_value_pm1_sub(w) : seeded_value_pm1(w);
+    } else {
+        return seeded_value(splitmix_mix(z), (double)lo, (double)span);
+    }
 }
 
-// The construction half: the tile's x (and y); the block's threads then meet so that every
-// input is in memory before the operation half (run_tile with coherent loads) reads it.
-__device__ __forceinline__ void construct_tile_inputs(const DevItem &it, uint64_t start, uint64_t cnt) {
-    const bool f64 = it.dtype == SX_F64;
-    const bool hy = it.op == SX_OP_ADD || it.op == SX_OP_TRIAD;
-    void *x = const_cast<void *>(it.x), *y = const_cast<void *>(it.y);
-    if (f64 && it.q2 == -1.0 && it.q3 == 1.0) {
-        tile_construct<double, true>(it, x, it.seed, start, cnt);
-        if (hy) tile_construct<double, true>(it, y, it.seed2, start, cnt);
-    } else if (f64) {
-        tile_construct<double, false>(it, x, it.seed, start, cnt);
-        if (hy) tile_construct<double, false>(it, y, it.seed2, start, cnt);
-    } else {
-        tile_construct<float, false>(it, x, it.seed, start, cnt);
-        if (hy) tile_construct<float, false>(it, y, it.seed2, start, cnt);
+template <int OP, class T, bool PM1, int MM>
+__device__ __forceinline__ void tile_fused(const DevItem &it, uint64_t start, uint64_t cnt) {
+    constexpr bool HY = has_y<OP>();
+    constexpr int E = 32 / (int)sizeof(T);  // elements per thread and step: one 32-byte vector per array
+    T *x = static_cast<T *>(const_cast<void *>(it.x)) + start;
+    T *y = HY ? static_cast<T *>(const_cast<void *>(it.y)) + start : nullptr;
+    T *o = static_cast<T *>(it.out) + start;
+    const T lo = (T)it.q2;
+    const T span = (T)it.q3 - lo;  // RN(hi - lo) in T, as the host-side generator defines it
+    const T q = (T)it.q;
+    const uint64_t base = it.index_base + start;  // generator index of element 0 of the tile
+    const uintptr_t mis = (uintptr_t)o % 32;
+    const bool vec_ok = ((uintptr_t)x % 32 == mis) && (!HY || (uintptr_t)y % 32 == mis) && mis % sizeof(T) == 0;
+    uint64_t head = vec_ok ? ((32 - mis) % 32) / sizeof(T) : cnt;
+    if (head > cnt) head = cnt;
+    const uint64_t nrun = (cnt - head) / E;
+    const uint64_t body_end = head + nrun * E;
+    for (uint64_t e = threadIdx.x; e < head + (cnt - body_end); e += blockDim.x) {
+        const uint64_t i = e < head ? e : body_end + (e - head);
+        const uint64_t z = (base + i + 1) * kSplitmixGamma;
+        const T xv = fused_input<T, PM1>(it.seed + z, lo, span, (int)i);
+        x[i] = xv;
+        T yv = T(0);
+        if constexpr (HY) {
+            yv = fused_input<T, PM1>(it.seed2 + z, lo, span, (int)i);
+            y[i] = yv;
+        }
+        o[i] = apply_op_mm<OP, MM, T>(xv, yv, q, (int)i);
     }
-    __syncthreads();  // the tile's inputs are in memory before any thread reads them
+    for (uint64_t r = threadIdx.x; r < nrun; r += blockDim.x) {
+        const uint64_t i0 = head + r * E;
+        const uint64_t z0 = (base + i0 + 1) * kSplitmixGamma;
+        T xv[E], yv[E], ov[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            xv[j] = fused_input<T, PM1>(it.seed + z0 + (uint64_t)j * kSplitmixGamma, lo, span, j);
+            yv[j] = T(0);
+            if constexpr (HY) yv[j] = fused_input<T, PM1>(it.seed2 + z0 + (uint64_t)j * kSplitmixGamma, lo, span, j);
+        }
+        stv<32, 0>(reinterpret_cast<char *>(x + i0), *reinterpret_cast<const uint64_t(*)[4]>(xv));
+        if constexpr (HY) stv<32, 0>(reinterpret_cast<char *>(y + i0), *reinterpret_cast<const uint64_t(*)[4]>(yv));
+#pragma unroll
+        for (int j = 0; j < E; ++j) ov[j] = apply_op_mm<OP, MM, T>(xv[j], yv[j], q, j);
+        stv<32, 0>(reinterpret_cast<char *>(o + i0), *reinterpret_cast<const uint64_t(*)[4]>(ov));
+    }
+}
+
+template <int OP>
+__device__ __forceinline__ void fused_tile_op(const DevItem &it, uint64_t start, uint64_t cnt) {
+    constexpr bool MUL = OP == SX_OP_SCALE || OP == SX_OP_TRIAD;
+    if (it.dtype != SX_F64) {
+        tile_fused<OP, float, false, 0>(it, start, cnt);
+    } else if (it.q2 == -1.0 && it.q3 == 1.0) {
+        if (MUL && it.mulv == 4) tile_fused<OP, double, true, 4>(it, start, cnt);
+        else if (MUL && it.mulv == 2) tile_fused<OP, double, true, 2>(it, start, cnt);
+        else tile_fused<OP, double, true, 0>(it, start, cnt);
+    } else {
+        if (MUL && it.mulv == 4) tile_fused<OP, double, false, 4>(it, start, cnt);
+        else if (MUL && it.mulv == 2) tile_fused<OP, double, false, 2>(it, start, cnt);
+        else tile_fused<OP, double, false, 0>(it, start, cnt);
+    }
+}
+
+__device__ __forceinline__ void fused_tile(const DevItem &it, uint64_t start, uint64_t cnt) {
+    switch (it.op) {
+        case SX_OP_COPY: fused_tile_op<SX_OP_COPY>(it, start, cnt); break;
+        case SX_OP_SCALE: fused_tile_op<SX_OP_SCALE>(it, start, cnt); break;
+        case SX_OP_ADD: fused_tile_op<SX_OP_ADD>(it, start, cnt); break;
+        case SX_OP_TRIAD: fused_tile_op<SX_OP_TRIAD>(it, start, cnt); break;
+        default: break;
+    }
 }
 
 template <int VB>
@@ -510,9 +574,8 @@ __global__ void __launch_bounds__(1024) k_batch_step(const __grid_constant__ Ste
         }
         const uint64_t start = (uint64_t)(t - p.prefix[lo]) * it.tile_elems;
         const uint64_t cnt = min((uint64_t)it.tile_elems, it.n - start);
-        const bool construct_first = (it.pad & kPadConstructThenOp) != 0;
-        if (construct_first) construct_tile_inputs(it, start, cnt);
-        run_tile<VB>(it, start, cnt, construct_first);
+        if (it.pad & kPadConstructThenOp) fused_tile(it, start, cnt);
+        else run_tile<VB>(it, start, cnt);
         const uint32_t w = it.pad >> 8;
         if (w) {
             // the piece's last finished tile publishes it (as the step's last block does below)

@@ -165,6 +165,12 @@ k_stream_bulk(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_
     __shared__ __align__(8) uint64_t empty[kMaxStages];
     __shared__ int abort_flag;
 
+    // launched as a programmatic dependent of the kernel before it on the stream (as the VECTOR
+    // kernels are): wait until that kernel has completed and its stores are visible, then let
+    // the next kernel's blocks be scheduled while this one runs
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
     // scalar edges: [0, head) and [head + nbody, n)
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t body_end = head + nbody;
@@ -294,6 +300,9 @@ k_stream_tma(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t
     __shared__ __align__(8) uint64_t done[kMaxStages];
     __shared__ __align__(8) uint64_t empty[kMaxStages];
     __shared__ int abort_flag;
+
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // as in k_stream_bulk
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     // scalar edges: [0, head) and [head + nbody, n) (up to 255 elements after the last row)
     const uint64_t body_end = head + nbody;
@@ -551,9 +560,22 @@ int launch_bulk_t(const sx_target *t, cudaStream_t st, const T *x, const T *y, T
     uint64_t grid = (uint64_t)t->sm_count * bps;
     if (grid > ntiles) grid = ntiles;
     if (grid == 0) grid = 1;
+    // programmatic dependent launch on the library's and callers' streams (the default streams
+    // keep plain serialisation), as for the VECTOR kernels
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3((unsigned)c.threads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = (st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread) ? 1 : 0;
+    cudaError_t e;
     if (c.variant == SX_VARIANT_BULK) {
-        bulk_kernel<OP, T>(mv)<<<(unsigned)grid, c.threads, smem, st>>>(x, y, out, n, head, nbody, tile_elems,
-                                                                        c.stages, q, t->d_err);
+        e = cudaLaunchKernelEx(&lc, bulk_kernel<OP, T>(mv), x, y, out, (uint64_t)n, (uint64_t)head, (uint64_t)nbody,
+                               tile_elems, c.stages, q, t->d_err);
     } else {
         TmaMaps maps;
         std::memset(&maps, 0, sizeof maps);
@@ -563,14 +585,14 @@ int launch_bulk_t(const sx_target *t, cudaStream_t st, const T *x, const T *y, T
             SX_TRY(encode_row_map(&maps.y, HAS_Y ? y + head : x + head, es, nrows, box_rows));
             SX_TRY(encode_row_map(&maps.out, out + head, es, nrows, box_rows));
         }
-        if (tensor)
-            tma_kernel<OP, T, true>(mv)<<<(unsigned)grid, c.threads, smem, st>>>(
-                x, y, out, n, head, nbody, tile_elems, c.stages, q, t->d_err, maps);
-        else
-            tma_kernel<OP, T, false>(mv)<<<(unsigned)grid, c.threads, smem, st>>>(
-                x, y, out, n, head, nbody, tile_elems, c.stages, q, t->d_err, maps);
+        e = cudaLaunchKernelEx(&lc, tensor ? tma_kernel<OP, T, true>(mv) : tma_kernel<OP, T, false>(mv), x, y, out,
+                               (uint64_t)n, (uint64_t)head, (uint64_t)nbody, tile_elems, c.stages, q, t->d_err, maps);
     }
-    SX_CUDA(cudaGetLastError());
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "bulk-copy kernel launch");
+    }
     return SX_OK;
 }
 

@@ -8,19 +8,22 @@
 // than the whole arena are rejected at submission.
 //
 // CONTINUOUS mode batches requests continuously.  A step is one launch of the batched kernel
-// (sx_batch.cu) over a list of pieces, passed in the launch's parameters: for active requests a
-// range of their current phase (phase 0 constructs x and y, phase 1 runs the operation).  The
-// step's byte budget goes by policy, shortest remaining work first by default, so short requests
-// finish in the first step that takes them while long ones advance in the rest.  Up to
-// steps_in_flight steps are queued on the stream and consecutive steps overlap through
-// programmatic dependent launch; a piece that needs the inputs built in a step not yet known
+// (sx_batch.cu) over a list of pieces, passed in the launch's parameters: for each active
+// request a range of its elements.  By default every piece is a construct-then-operate piece:
+// each tile builds its range of the inputs from their seeds and then applies the operation to
+// it, reading the inputs back while they are still in L2, so the integer-bound construction of
+// one block overlaps the memory-bound operations of others on the same SM, and the operation's
+// input reads do not go to DRAM.  (With split_phases, as before, phase 0 constructs x and y and
+// phase 1 runs the operation in a later piece; only short requests are fused.)  The step's byte
+// budget goes by policy, shortest remaining work first by default, so short requests finish in
+// the first step that takes them while long ones advance in the rest.  Up to steps_in_flight
+// steps are queued on the stream and consecutive steps overlap through programmatic dependent
+// launch; a split-phase operation piece that needs the inputs built in a step not yet known
 // complete waits for it on the device.  The thread builds the next step while the GPU runs the
 // previous ones, admits arrivals between steps, and marks a request DONE when the step holding
-// its last piece has completed.  A short request (its whole work at most a quarter of a step's
-// budget) that a step takes whole runs as one construct-then-operate piece (each tile builds its
-// range of the inputs, then applies the operation to it) and reports its own completion: the
-// block that finishes its last tile sets a host-mapped word, and the request is DONE as soon as
-// the thread sees it, without waiting for the rest of the step.
+// its last piece has completed.  A request that a step takes whole, in one piece, reports its
+// own completion: the block that finishes the piece's last tile sets a host-mapped word, and the
+// request is DONE as soon as the thread sees it, without waiting for the rest of the step.
 //
 // FIFO mode is the per-call baseline: each admitted request is enqueued at once as its own
 // launches (construct x, construct y, operation) in arrival order, like a client calling the
@@ -278,15 +281,19 @@ int launch_step(sx_server *s, bool *launched) {
     std::vector<sched::Want> w;
     std::vector<Request *> by_key;
     std::vector<uint8_t> whole;  // short and not started: planned with the bytes of both phases
+    const bool split = s->cfg.split_phases != 0;
     for (Request *q : s->active) {
         if (q->phase >= 2) continue;
         const uint64_t p0 = phase_bytes_per_elem(*q, 0), p1 = phase_bytes_per_elem(*q, 1);
-        const bool short_whole = q->phase == 0 && q->next == 0 && (uint64_t)q->r.n * (p0 + p1) <= budget / 4;
-        const uint64_t later = q->phase == 0 && !short_whole ? (uint64_t)q->r.n * p1 : 0;
-        const uint64_t per = short_whole ? p0 + p1 : phase_bytes_per_elem(*q, q->phase);
+        // fused: every piece constructs its range of the inputs and applies the operation to it;
+        // split: short requests (whole work at most a quarter of the budget) as one such piece,
+        // the others in two phases
+        const bool fused = !split || (q->phase == 0 && q->next == 0 && (uint64_t)q->r.n * (p0 + p1) <= budget / 4);
+        const uint64_t later = q->phase == 0 && !fused ? (uint64_t)q->r.n * p1 : 0;
+        const uint64_t per = fused ? p0 + p1 : phase_bytes_per_elem(*q, q->phase);
         w.push_back({by_key.size(), q->admit_seq, per, q->r.n - q->next, later});
         by_key.push_back(q);
-        whole.push_back(short_whole ? 1 : 0);
+        whole.push_back(fused ? 1 : 0);
     }
     if (w.empty()) return SX_OK;
     // elements of each request's current phase in this step, in the policy's order (sx_sched.h)
@@ -306,23 +313,25 @@ int launch_step(sx_server *s, bool *launched) {
         const uint64_t lo = q->next, hi = lo + elems;
         const sx_request &r = q->r;
         const size_t es = dtype_size(r.dtype);
-        if (whole[w[i].key] && elems == r.n) {
-            // the whole request in one piece: construct x (and y), then the operation
+        if (whole[w[i].key] && (!split || elems == r.n)) {
+            // construct x (and y) over [lo, hi), then the operation on that range, tile by tile
             StepItem si;
             si.item.op = r.op;
             si.item.dtype = r.dtype;
-            si.item.n = r.n;
-            si.item.x = ptr_of(s, q, 0);
-            si.item.y = ptr_of(s, q, 1);
-            si.item.out = ptr_of(s, q, 2);
+            si.item.n = elems;
+            si.item.x = (char *)ptr_of(s, q, 0) + lo * es;
+            si.item.y = has_y(r.op) ? (char *)ptr_of(s, q, 1) + lo * es : nullptr;
+            si.item.out = (char *)ptr_of(s, q, 2) + lo * es;
             si.item.q = r.q;
             si.item.q2 = r.lo;
             si.item.seed = r.seed_x;
-            si.item.index_base = 0;
+            si.item.index_base = lo;
             si.flags = kStepConstructThenOp;
             si.seed2 = r.seed_y;
             si.hi = r.hi;
-            if (!s->free_fin.empty()) {
+            const bool one_piece = lo == 0 && elems == r.n;
+            if (one_piece && !s->free_fin.empty()) {
+                // the whole request in this piece: it reports its own completion
                 q->fin_word = s->free_fin.back();
                 s->free_fin.pop_back();
                 ((volatile unsigned long long *)s->fin_host)[q->fin_word] = 0;
@@ -331,10 +340,14 @@ int launch_step(sx_server *s, bool *launched) {
                 watch.push_back(q);
             }
             items.push_back(si);
-            st.bytes += (uint64_t)r.n * (phase_bytes_per_elem(*q, 0) + phase_bytes_per_elem(*q, 1));
-            q->phase = 2;
-            st.finishing.push_back(q);
-            s->stats.fused++;
+            st.bytes += elems * (phase_bytes_per_elem(*q, 0) + phase_bytes_per_elem(*q, 1));
+            q->next = hi;
+            if (q->next == r.n) {
+                q->next = 0;
+                q->phase = 2;
+                st.finishing.push_back(q);
+            }
+            if (one_piece) s->stats.fused++;
             continue;
         }
         const uint64_t per = phase_bytes_per_elem(*q, q->phase);
@@ -707,12 +720,18 @@ int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out) {
         return fail(SX_ERR_INVALID, "policy %d", c.policy);
     if (c.serialize_steps != 0 && c.serialize_steps != 1)
         return fail(SX_ERR_INVALID, "serialize_steps %d: 0 or 1", c.serialize_steps);
+    if (c.split_phases != 0 && c.split_phases != 1)
+        return fail(SX_ERR_INVALID, "split_phases %d: 0 or 1", c.split_phases);
     if (c.max_active < 1 || c.max_active > 65536) return fail(SX_ERR_INVALID, "max_active %d", c.max_active);
     if (c.chunk_bytes < (1 << 20)) return fail(SX_ERR_INVALID, "chunk_bytes %d below 1 MiB", c.chunk_bytes);
     if (c.steps_in_flight < 1 || c.steps_in_flight > 8) return fail(SX_ERR_INVALID, "steps_in_flight %d", c.steps_in_flight);
+    // default step-kernel shape, measured on the served workload with construct-then-operate
+    // pieces: four blocks of 256 threads per SM (the kernel's 63 registers allow 1024 threads),
+    // so that blocks constructing (integer-bound) and blocks operating (memory-bound) share each
+    // SM, and 128 KiB tiles, whose inputs are still in L2 when the tile's operation reads them
     sx_batch_cfg k{};
-    k.chunk_bytes = c.tile_bytes ? c.tile_bytes : 256 * 1024;
-    k.threads = c.threads ? c.threads : 512;
+    k.chunk_bytes = c.tile_bytes ? c.tile_bytes : 128 * 1024;
+    k.threads = c.threads ? c.threads : 256;
     k.blocks_per_sm = c.blocks_per_sm ? c.blocks_per_sm : 4;
     k.vec_bytes = c.vec_bytes ? c.vec_bytes : 32;
     if (k.chunk_bytes < 16384 || k.threads % 32 || k.threads < 64 || k.threads > 1024 ||

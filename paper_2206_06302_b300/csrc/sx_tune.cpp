@@ -192,17 +192,19 @@ sx_launch_cfg resolve_cfg(const sx_target *t, int op, int dtype, size_t n, const
         if (c.threads == 0) c.threads = 256;
         if (c.vec_bytes == 0) c.vec_bytes = 32;
         if (c.unroll == 0) c.unroll = 2;
-    } else if (c.variant == SX_VARIANT_BULK) {
-        if (c.threads == 0) c.threads = 256;
-        if (c.blocks_per_sm == 0) c.blocks_per_sm = 1;
-        if (c.tile_bytes == 0) c.tile_bytes = 16384;
-        if (c.stages == 0) c.stages = 4;
-    } else if (c.variant == SX_VARIANT_TMA || c.variant == SX_VARIANT_TMA_TENSOR) {
-        // the shape that did best over the four kernels at 2^27 (blocks per SM capped by shared memory)
-        if (c.threads == 0) c.threads = op == SX_OP_COPY ? 96 : 256;
-        if (c.blocks_per_sm == 0) c.blocks_per_sm = 4;
-        if (c.tile_bytes == 0) c.tile_bytes = 8192;
-        if (c.stages == 0) c.stages = 4;
+    } else if (c.variant == SX_VARIANT_BULK || c.variant == SX_VARIANT_TMA || c.variant == SX_VARIANT_TMA_TENSOR) {
+        // each family's fastest shape per kernel at n = 2^27 (binary64, measured on B300 over the
+        // tuner's candidates): threads, blocks per SM, tile bytes, stages
+        static const int kShape[3][4][4] = {
+            // copy                scale                 add                  triad
+            {{128, 1, 32768, 2}, {512, 1, 32768, 3}, {256, 1, 16384, 3}, {128, 4, 8192, 2}},  // BULK
+            {{96, 3, 8192, 3}, {512, 2, 32768, 4}, {512, 2, 8192, 4}, {256, 4, 8192, 3}},     // TMA
+            {{96, 1, 32768, 3}, {512, 3, 32768, 4}, {512, 2, 8192, 4}, {256, 4, 8192, 3}}};   // TMA_TENSOR
+        const int *d = kShape[c.variant - SX_VARIANT_BULK][(op >= SX_OP_COPY && op <= SX_OP_TRIAD) ? op : SX_OP_TRIAD];
+        if (c.threads == 0) c.threads = d[0];
+        if (c.blocks_per_sm == 0) c.blocks_per_sm = d[1];
+        if (c.tile_bytes == 0) c.tile_bytes = d[2];
+        if (c.stages == 0) c.stages = d[3];
     }
     return c;
 }

@@ -79,7 +79,8 @@ class sx_server_cfg(C.Structure):
     _fields_ = [("budget_bytes", C.c_uint64), ("mode", C.c_int32), ("max_active", C.c_int32),
                 ("chunk_bytes", C.c_int32), ("steps_in_flight", C.c_int32),
                 ("threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("vec_bytes", C.c_int32),
-                ("tile_bytes", C.c_int32), ("policy", C.c_int32), ("serialize_steps", C.c_int32)]
+                ("tile_bytes", C.c_int32), ("policy", C.c_int32), ("serialize_steps", C.c_int32),
+                ("split_phases", C.c_int32)]
 
 
 class sx_request(C.Structure):

@@ -63,13 +63,15 @@ def test_each_request_alone(target, mode):
     sx.sx_server_destroy(s)
 
 
-@pytest.mark.parametrize("mode", [sx.SX_SERVE_CONTINUOUS, sx.SX_SERVE_FIFO])
-def test_mix_equals_alone(target, mode):
+@pytest.mark.parametrize("mode,split", [(sx.SX_SERVE_CONTINUOUS, 0), (sx.SX_SERVE_CONTINUOUS, 1),
+                                        (sx.SX_SERVE_FIFO, 0)])
+def test_mix_equals_alone(target, mode, split):
     """200 requests of mixed op, type and length arrive together; small step budget and tiles
-    make long requests span many steps and share them with short ones."""
+    make long requests span many steps and share them with short ones (as construct-then-operate
+    ranges, or with split_phases in two phases)."""
     reqs = _requests(200, seed=4)
     s = sx.sx_server_create(target, budget_bytes=256 << 20, mode=mode, chunk_bytes=1 << 20,
-                            tile_bytes=16384, max_active=64, steps_in_flight=2)
+                            tile_bytes=16384, max_active=64, steps_in_flight=2, split_phases=split)
     ids = [sx.sx_server_submit(s, **r) for r in reqs]
     _check_all(s, ids, reqs, "mix")
     st = sx.sx_server_stats_get(s)
@@ -80,11 +82,13 @@ def test_mix_equals_alone(target, mode):
     sx.sx_server_destroy(s)
 
 
-def test_short_requests_run_whole_and_report_early(target):
-    """Requests whose whole work fits a quarter of the step budget run as one construct-then-
-    operate piece and complete from that piece's own report, while the long request sharing their
-    steps goes on; longer ones run in two phases.  Every result is the oracle's."""
-    s = sx.sx_server_create(target, budget_bytes=8 << 30, chunk_bytes=1 << 30)
+@pytest.mark.parametrize("split", [0, 1])
+def test_short_requests_run_whole_and_report_early(target, split):
+    """Requests that a step takes whole run as one construct-then-operate piece and complete from
+    that piece's own report, while the long request sharing their steps goes on in ranges (with
+    split_phases only requests within a quarter of the step budget run whole; longer ones run in
+    two phases).  Every result is the oracle's."""
+    s = sx.sx_server_create(target, budget_bytes=8 << 30, chunk_bytes=1 << 30, split_phases=split)
     long_r = dict(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=1 << 27, q=3.0, seed_x=91, seed_y=92,
                   lo=-1.0, hi=1.0)  # 5 GiB of work: several 1 GiB steps of ~0.15 ms
     mid_r = dict(op=sx.SX_OP_ADD, dtype=sx.SX_F32, n=20 << 20, q=1.0, seed_x=93, seed_y=94,
@@ -97,8 +101,26 @@ def test_short_requests_run_whole_and_report_early(target):
     sids = [sx.sx_server_submit(s, **r) for r in shorts]
     _check_all(s, sids + [mid, lid], shorts + [mid_r, long_r], "short and long")
     st = sx.sx_server_stats_get(s)
-    assert st["fused"] == len(shorts), st
+    # the first step takes the shorts and the mid request whole (SRPT), the long one in ranges
+    assert st["fused"] == len(shorts) + (0 if split else 1), st
     assert 1 <= st["early_done"] <= st["fused"], st
+    sx.sx_server_destroy(s)
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_single_request_in_one_or_two_steps(target, split):
+    """One FP64 triad request of 2^24 elements (640 MiB of work) with a 2 GiB step budget: by
+    default one construct-then-operate step (its inputs computed in registers, stored, and the
+    operation applied to them), with split_phases a construction step and then an operation
+    step (the request is over a quarter of the budget).  Both leave the oracle's inputs and
+    result."""
+    r = dict(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=1 << 24, q=3.0, seed_x=11, seed_y=12, lo=-1.0, hi=1.0)
+    s = sx.sx_server_create(target, budget_bytes=1 << 30, chunk_bytes=(2 << 30) - 1, split_phases=split)
+    rid = sx.sx_server_submit(s, **r)
+    _check_all(s, [rid], [r], f"split_phases={split}")
+    st = sx.sx_server_stats_get(s)
+    assert st["steps"] == (2 if split else 1) and st["fused"] == (0 if split else 1), st
+    assert st["bytes_moved"] == 40 * (1 << 24)
     sx.sx_server_destroy(s)
 
 

@@ -50,6 +50,10 @@ CFGS = [
          fp64_mul=1),
     dict(variant=sx.SX_VARIANT_TMA_TENSOR, threads=256, blocks_per_sm=1, tile_bytes=16384, stages=4,
          fp64_mul=2),
+    # each family's default shape (zero fields: the per-kernel shapes measured fastest at 2^27)
+    dict(variant=sx.SX_VARIANT_BULK, fp64_mul=2),
+    dict(variant=sx.SX_VARIANT_TMA, fp64_mul=2),
+    dict(variant=sx.SX_VARIANT_TMA_TENSOR, fp64_mul=2),
 ]
 
 
