@@ -436,9 +436,11 @@ def served_summary(s):
             per[f"{ld:g}"] = {"p50_ms": [c["p50_ms"], f["p50_ms"]], "p99_ms": [c["p99_ms"], f["p99_ms"]],
                               "GB/s": [c["GB/s"], f["GB/s"]]}
     sat = s["saturation_GB/s"]
-    return {"what": "continuous batching vs per-call FIFO; per load [continuous, fifo]",
+    return {"what": "continuous batching vs per-call FIFO; per load [continuous, fifo]; GB/s in STREAM bytes "
+                    "(input construction and operation)",
             "saturation_GB/s": sat, "saturation_runs_GB/s": s.get("saturation_runs_GB/s"),
             "saturation_frac_measured": s.get("saturation_frac_measured"),
+            "saturation_dram_GB/s": s.get("saturation_dram_GB/s"),
             "saturation_gain": round(sat["continuous"] / sat["fifo"], 4) if sat.get("fifo") else None,
             "loads": per,
             "beats_fifo": {"throughput": sat["continuous"] > sat["fifo"],
@@ -465,18 +467,26 @@ def serve_run(sx, t, work, times, budget_bytes, mode, server_kw=None):
     return lat, stats, (t1 - t0) if t1 is not None else float("nan")
 
 
-def served_workload(sx, seed, count):
-    """The served requests (sx_request list), their element counts and STREAM byte counts."""
+def served_workload(sx, seed, count, dram=None):
+    """The served requests (sx_request list), their element counts and STREAM byte counts.  If
+    `dram` is a dict, it receives the workload's total DRAM bytes under each mode: "continuous"
+    (every piece stores x, y and out and reads nothing back) and "fifo" (the operation reads the
+    inputs back from DRAM)."""
     import stream_inputs as si
     reqs = si.poisson_requests(seed, count, rate_per_s=1.0)
     ops = {"copy": sx.SX_OP_COPY, "scale": sx.SX_OP_SCALE, "add": sx.SX_OP_ADD, "triad": sx.SX_OP_TRIAD}
     dts = {"f64": (sx.SX_F64, 8), "f32": (sx.SX_F32, 4)}
     work, nbytes = [], []
+    written = read = 0
     for r in reqs:
         code, es = dts[r["dtype"]]
         two = r["op"] in ("add", "triad")
         # inputs construction (x, and y for add/triad) plus the operation itself
         nbytes.append(r["n"] * es * ((2 if two else 1) + (3 if two else 2)))
+        written += r["n"] * es * ((2 if two else 1) + 1)
+        read += r["n"] * es * (2 if two else 1)
+        if dram is not None:
+            dram["continuous"], dram["fifo"] = written, written + read
         work.append(sx.sx_request(op=ops[r["op"]], dtype=code, n=r["n"], q=Q,
                                   seed_x=si.word_scalar(r["seed"], 0), seed_y=si.word_scalar(r["seed"], 1),
                                   lo=-1.0, hi=1.0, flags=sx.SX_REQ_AUTO_RELEASE))
@@ -491,7 +501,8 @@ def served_section(sx, torch, t, stream, args, rank):
     loads of 0.5, 0.8 and 0.95 of that capacity: p50/p99 latency (submission to completion seen
     by the server), the p99 of the shorter half of the requests, and throughput."""
     import stream_inputs as si
-    reqs, work, nbytes = served_workload(sx, si.BASE_SEED + 7 + rank, args.serve_count)
+    dram = {}
+    reqs, work, nbytes = served_workload(sx, si.BASE_SEED + 7 + rank, args.serve_count, dram)
     mean_bytes = sum(nbytes) / len(nbytes)
     budget = int(args.serve_budget_gb * 1e9)
     median_n = sorted(r["n"] for r in reqs)[len(reqs) // 2]
@@ -515,6 +526,9 @@ def served_section(sx, torch, t, stream, args, rank):
         out["saturation_GB/s"][name] = round(max(runs), 1)
         out.setdefault("saturation_runs_GB/s", {})[name] = [round(v, 1) for v in runs]
         out.setdefault("saturation_frac_measured", {})[name] = round(max(runs) / _measured_peaks()[0], 4)
+        # the DRAM traffic each mode has to move for the same work, at that rate
+        out.setdefault("saturation_dram_GB/s", {})[name] = round(max(runs) * dram[name] / sum(nbytes), 1)
+    out["dram_bytes_per_stream_byte"] = {k: round(v / sum(nbytes), 4) for k, v in dram.items()}
     capacity = out["saturation_GB/s"]["fifo"] * 1e9
     out["capacity_from"] = "per-call FIFO throughput at saturation"
     for load in [float(v) for v in args.serve_loads.split(",") if v]:
@@ -532,6 +546,40 @@ def served_section(sx, torch, t, stream, args, rank):
                 "launches": stats["launches"], "steps": stats["steps"],
                 "rejected": len(lat) - len(done), "arena_peak_GB": round(stats["arena_peak"] / 1e9, 2)})
     return out
+
+
+def dram_mix_section(sx, torch, t, stream, execs, n, reps=20):
+    """The DRAM rate by read/write mix, with the library's own kernels on three FP64 arrays of n
+    elements: sx_bulk_construct's fill (stores only), copy (one read per write) and add (two
+    reads per write).  Each launch between its own CUDA events on the launching stream; the
+    median of `reps` after 3 untimed ones.  Copy's rate is bounded by the DRAM's mixed-direction
+    rate, which this shows beside the store-only rate."""
+    arrs = [sx.sx_alloc(t, sx.SX_F64, n) for _ in range(3)]
+    for k, a in enumerate(arrs):
+        sx.sx_seed_uniform(a, k + 1, -1.0, 1.0)
+    x, y, o = arrs
+
+    def median_ms(fn):
+        for _ in range(3):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sorted(a.elapsed_time(b) for a, b in ev)[reps // 2]
+
+    ms = {"fill": median_ms(lambda: sx.sx_bulk_construct(o, 1.5)),
+          "copy": median_ms(lambda: sx.sx_execute_async(execs[sx.SX_OP_COPY], sx.SX_OP_COPY, x, None, o, Q, future=False)),
+          "add": median_ms(lambda: sx.sx_execute_async(execs[sx.SX_OP_ADD], sx.SX_OP_ADD, x, y, o, Q, future=False))}
+    for a in arrs:
+        sx.sx_free(a)
+    nb = n * 8
+    return {"what": f"FP64 arrays of n={n}; median per-launch device time of {reps}",
+            "fill_stores_only_GB/s": round(nb / (ms["fill"] * 1e-3) / 1e9, 1),
+            "copy_1_read_1_write_GB/s": round(2 * nb / (ms["copy"] * 1e-3) / 1e9, 1),
+            "add_2_reads_1_write_GB/s": round(3 * nb / (ms["add"] * 1e-3) / 1e9, 1)}
 
 
 def fused_section(sx, torch, t, stream, n, rank, passes=100):
@@ -867,6 +915,26 @@ def run_sweep(args):
     return 0
 
 
+def run_dram_mix(args):
+    """The DRAM mix on its own, in a fresh process (see dram_mix_section): one JSON line.  The
+    FP64 launch shapes are the tuner table's for --n."""
+    import torch
+    import paper_2206_06302_b300 as sx
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    t = sx.target_on_torch_stream(0, stream)
+    e_auto = sx.sx_executor_create(t, sx.SX_PAR_TASK)
+    execs = {op: sx.sx_executor_create(t, sx.SX_PAR_TASK, sx.sx_executor_resolve(e_auto, op, sx.SX_F64, args.n))
+             for op in (sx.SX_OP_COPY, sx.SX_OP_ADD)}
+    out = dram_mix_section(sx, torch, t, stream, execs, args.n)
+    out["device"] = sx.sx_target_info_get(t)["name"]
+    print(json.dumps({"dram_mix": out}), flush=True)
+    for e in list(execs.values()) + [e_auto]:
+        sx.sx_executor_destroy(e)
+    sx.sx_target_destroy(t)
+    return 0
+
+
 def run_ours(args):
     import torch
     import paper_2206_06302_b300 as sx
@@ -1126,6 +1194,9 @@ def main(argv=None):
                     help="double a once after construction, as classic STREAM does before timing")
     ap.add_argument("--variant", choices=["auto", "vector", "bulk", "tma", "tma_tensor"], default="auto",
                     help="kernel family of the timed passes (auto: the tuner table)")
+    ap.add_argument("--dram-mix", action="store_true",
+                    help="instead of the step benchmark: the DRAM rate of stores only (fill), one read per "
+                         "write (copy) and two reads per write (add) on FP64 arrays of --n elements")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the step benchmark: the size sweep, vector vs the two TMA bulk-copy families")
     ap.add_argument("--sweep-lo", type=int, default=10)
@@ -1158,6 +1229,8 @@ def main(argv=None):
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.dram_mix:
+        return run_dram_mix(args)
     return run_ours(args)
 
 

@@ -26,28 +26,69 @@ unsigned seed_blocks(size_t n, int per_thread) {
     return b == 0 ? 1u : (unsigned)b;
 }
 
+// ---- construction with one value: stores only ------------------------------------------------
+// Elements [0, head) and [head + nvec * 32 / sizeof(T), n) one by one by the first threads of the
+// grid; the body is nvec 32-byte vector stores of `word` (the value's bits repeated over 8 bytes),
+// in tiles of two stores per thread, one tile per block (a grid-stride loop over tiles only
+// beyond 2^31 blocks).  Measured on B300 at 1 GiB: one tile per block 7.3 TB/s, a grid-stride
+// loop over 16 blocks per SM 6.8 TB/s.
+constexpr int kFillThreads = 256, kFillUnroll = 2;
 template <class T>
-__global__ void k_fill(T *out, uint64_t n, T v) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = v;
+__global__ void __launch_bounds__(kFillThreads) k_fill(T *out, uint64_t n, uint64_t head, uint64_t nvec, T v,
+                                                       uint64_t word) {
+    constexpr uint64_t EPV = 32 / sizeof(T);
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t body_end = head + nvec * EPV;
+    if (gtid < head + (n - body_end)) out[gtid < head ? gtid : body_end + (gtid - head)] = v;
+    char *b = reinterpret_cast<char *>(out + head);
+    const uint64_t w[4] = {word, word, word, word};
+    const uint64_t tile = (uint64_t)blockDim.x * kFillUnroll;
+    for (uint64_t base = (uint64_t)blockIdx.x * tile; base < nvec; base += (uint64_t)gridDim.x * tile) {
+#pragma unroll
+        for (int u = 0; u < kFillUnroll; ++u) {
+            const uint64_t k = base + (uint64_t)u * blockDim.x + threadIdx.x;
+            if (k < nvec) stv<32, 0>(b + 32 * k, w);
+        }
+    }
 }
 
-unsigned setup_blocks(size_t n) {
-    uint64_t b = (n + 255) / 256;
-    if (b > 148ull * 32) b = 148ull * 32;
-    return b == 0 ? 1u : (unsigned)b;
+template <class T>
+int fill_t(cudaStream_t s, T *out, size_t n, T v, uint64_t word) {
+    const uintptr_t mis = (uintptr_t)out % 32;
+    uint64_t head = mis % sizeof(T) ? n : ((32 - mis) % 32) / sizeof(T);
+    if (head > n) head = n;
+    const uint64_t nvec = (n - head) * sizeof(T) / 32;
+    const uint64_t edge = n - nvec * 32 / sizeof(T);
+    const uint64_t tile = (uint64_t)kFillThreads * kFillUnroll;
+    uint64_t b = (nvec + tile - 1) / tile;
+    if (b > 0x7fffffffull) b = 0x7fffffffull;  // then a grid-stride loop over the tiles
+    const uint64_t eb = (edge + kFillThreads - 1) / kFillThreads;
+    if (b < eb) b = eb;
+    if (b == 0) b = 1;
+    if (b > 0x7fffffffull) return fail(SX_ERR_INVALID, "bulk_construct: array too long for its edge elements");
+    k_fill<T><<<(unsigned)b, kFillThreads, 0, s>>>(out, n, head, nvec, v, word);
+    return SX_OK;
 }
 
 }  // namespace
 
 int launch_fill(cudaStream_t s, int dtype, void *out, size_t n, double value) {
     if (n == 0) return SX_OK;
-    const unsigned b = setup_blocks(n);
-    if (dtype == SX_F64) k_fill<double><<<b, 256, 0, s>>>((double *)out, n, value);
-    else if (dtype == SX_F32) k_fill<float><<<b, 256, 0, s>>>((float *)out, n, (float)value);
-    else if (dtype == SX_U8) k_fill<uint8_t><<<b, 256, 0, s>>>((uint8_t *)out, n, (uint8_t)value);
-    else return fail(SX_ERR_DTYPE, "bulk_construct: unsupported dtype %d", dtype);
+    if (dtype == SX_F64) {
+        uint64_t w;
+        std::memcpy(&w, &value, 8);
+        SX_TRY(fill_t<double>(s, (double *)out, n, value, w));
+    } else if (dtype == SX_F32) {
+        const float f = (float)value;
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        SX_TRY(fill_t<float>(s, (float *)out, n, f, ((uint64_t)u << 32) | u));
+    } else if (dtype == SX_U8) {
+        const uint8_t c = (uint8_t)value;
+        SX_TRY(fill_t<uint8_t>(s, (uint8_t *)out, n, c, 0x0101010101010101ull * c));
+    } else {
+        return fail(SX_ERR_DTYPE, "bulk_construct: unsupported dtype %d", dtype);
+    }
     SX_CUDA(cudaGetLastError());
     return SX_OK;
 }

@@ -1,0 +1,48 @@
+"""Host logic of bench.py, on CPU: the reconstruction count inside the timed passes, the compact
+batched and served comparisons that close the JSON line, and the served workload's byte
+accounting (STREAM bytes against the DRAM bytes of each serving mode)."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_reseeds_between():
+    assert bench.reseeds_between(5, 20) == 0
+    assert bench.reseeds_between(0, 100) == 0 and bench.reseeds_between(0, 101) == 1
+    assert bench.reseeds_between(95, 10) == 1 and bench.reseeds_between(5, 1000) == 10
+
+
+def test_served_summary():
+    runs = [dict(mode=m, offered_load=ld, p50_ms=p50, p99_ms=p99, **{"GB/s": g})
+            for m, ld, p50, p99, g in (("continuous", 0.5, 0.1, 1.0, 10.0), ("fifo", 0.5, 0.2, 2.0, 10.0),
+                                        ("continuous", 0.9, 0.1, 3.0, 18.0), ("fifo", 0.9, 5.0, 2.5, 17.0))]
+    s = bench.served_summary({"runs": runs, "saturation_GB/s": {"continuous": 8.0, "fifo": 5.0}})
+    assert s["saturation_gain"] == 1.6 and s["beats_fifo"]["throughput"]
+    assert s["loads"]["0.5"]["p99_ms"] == [1.0, 2.0] and s["loads"]["0.9"]["GB/s"] == [18.0, 17.0]
+    assert not s["beats_fifo"]["p99_every_load"]  # 3.0 > 2.5 at 0.9
+
+
+def test_batched_summary():
+    b = {"workload": "w", "graph_ms": 1.0, "percall_ms": 2.0, "graph_GB/s": 10.0, "percall_GB/s": 5.0,
+         "speedup": 2.0, "completion_ms_p50": {"graph": 0.5, "percall": 1.0},
+         "completion_ms_p99": {"graph": 0.9, "percall": 1.9}, "graph_equals_percall_8_instances": True,
+         "noalloc": {"device_ms": 1.1, "host_us_per_call_median": 900.0, "graph_launch_host_us_median": 2.0}}
+    s = bench.batched_summary(b)
+    assert s["beats_percall"] == {"throughput": True, "p99": True} and s["noalloc_host_us_per_call"] == 900.0
+
+
+def test_served_workload_byte_accounting():
+    import paper_2206_06302_b300 as sx
+    dram = {}
+    reqs, work, nbytes = bench.served_workload(sx, 99, 300, dram)
+    assert len(work) == len(nbytes) == 300
+    # the per-call FIFO moves every STREAM byte through DRAM; construct-then-operate pieces only
+    # store (x, y, out): 3 of 5 arrays for add/triad, 2 of 3 for copy/scale
+    assert dram["fifo"] == sum(nbytes)
+    written = sum(r["n"] * (8 if r["dtype"] == "f64" else 4) * (3 if r["op"] in ("add", "triad") else 2)
+                  for r in reqs)
+    assert dram["continuous"] == written < dram["fifo"]

@@ -12,7 +12,7 @@ import pytest
 import oracle
 import paper_2206_06302_b300 as sx
 import stream_inputs as si
-from gpu_util import assert_bitwise, bits, empty, to_device, to_host
+from gpu_util import CODE, assert_bitwise, bits, empty, to_device, to_host
 from test_oracle_pins import rounding_cases
 
 pytestmark = pytest.mark.gpu
@@ -483,6 +483,33 @@ def test_bulk_construct_fill(target):
         sx.sx_bulk_destroy(d)  # Listing 1's pair to bulk_construct; frees nothing
         assert sx.sx_array_data(d)[1] == 1001
         sx.sx_free(d)
+    # the value converted to the element type once, every element its bits (32-byte vector stores
+    # in the body, element stores at a misaligned head and a ragged tail), nothing written past
+    # the end of the array or outside a borrowed view
+    values = {np.float64: (-0.0, 5e-324, float("inf"), 1.0 / 3.0), np.float32: (-0.0, 1e-45, float("-inf"), 1.0 / 3.0),
+              np.uint8: (0.0, 97.0, 255.0)}
+    for dt, vals in values.items():
+        es = np.dtype(dt).itemsize
+        for n in (1, 3, 31, 33, 4099, (1 << 20) + 5):
+            for v in vals:
+                want = np.full(n, v, dt) if dt != np.uint8 else np.full(n, int(v), dt)
+                d = empty(target, dt, n)
+                sx.sx_bulk_construct(d, v)
+                assert_bitwise(to_host(d), want, f"fill {dt.__name__} n={n} v={v}")
+                assert sx.sx_array_guard_ok(d)
+                sx.sx_free(d)
+        # a view starting off the 32-byte boundary inside a larger array of sentinels
+        n = 5000
+        big = to_device(target, np.full(n + 64, 7, dt))
+        base = sx.sx_array_data(big)[0]
+        for off in (1, 3, 5):
+            view = sx.sx_array_wrap(target, CODE[np.dtype(dt)], base + off * es, n)
+            sx.sx_bulk_construct(view, 1.0)
+            got = to_host(big)
+            assert np.all(got[off:off + n] == 1) and np.all(got[:off] == 7) and np.all(got[off + n:] == 7), off
+            sx.sx_bulk_construct(view, 7.0)
+            sx.sx_free(view)
+        sx.sx_free(big)
     with pytest.raises(sx.SxError) as ei:
         sx.sx_bulk_destroy(None)
     assert ei.value.status == sx.SX_ERR_INVALID
