@@ -578,11 +578,14 @@ __global__ void __launch_bounds__(1024) k_batch_step(const __grid_constant__ Ste
         else run_tile<VB>(it, start, cnt);
         const uint32_t w = it.pad >> 8;
         if (w) {
-            // the piece's last finished tile publishes it (as the step's last block does below)
-            __syncthreads();
-            if (threadIdx.x == 0) {
+            // Each warp counts its part of the tile (no block-wide barrier per tile): its lanes'
+            // stores are ordered before lane 0's device-scope fence, and the last of the piece's
+            // ntiles x warps parts publishes it (as the step's last block does below).
+            __syncwarp();
+            if ((threadIdx.x & 31u) == 0) {
                 __threadfence();
-                if (atomicAdd(p.fin_count + (w - 1), 1u) == it.ntiles - 1) {
+                const uint32_t parts = it.ntiles * (blockDim.x >> 5);
+                if (atomicAdd(p.fin_count + (w - 1), 1u) == parts - 1) {
                     p.fin_count[w - 1] = 0u;
                     __threadfence_system();
                     *(volatile unsigned long long *)(p.fin_host + (w - 1)) = 1ull;
@@ -658,6 +661,8 @@ int step_launch(const sx_target *t, cudaStream_t stream, StepSlot &s, const Step
             if ((uint64_t)tiles + nti > 0xffffffffull) return fail(SX_ERR_INVALID, "step has too many tiles");
             if (si.fin_word && (!report || !report->fin_host || si.fin_word >= (1u << 24)))
                 return fail(SX_ERR_INVALID, "piece completion word without report words");
+            if (si.fin_word && nti * (uint64_t)(cfg.threads / 32) >= (1ull << 32))
+                return fail(SX_ERR_INVALID, "piece with a completion word has too many tiles");
             d.pad = (si.flags & kStepDependent ? kPadDependent : 0u) |
                     (si.flags & kStepConstructThenOp ? kPadConstructThenOp : 0u) | (si.fin_word << 8);
             p.prefix[i] = tiles;
