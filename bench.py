@@ -437,7 +437,8 @@ def served_summary(s):
                               "GB/s": [c["GB/s"], f["GB/s"]]}
     sat = s["saturation_GB/s"]
     return {"what": "continuous batching vs per-call FIFO; per load [continuous, fifo]; GB/s in STREAM bytes "
-                    "(input construction and operation)",
+                    "(input construction and operation); continuous_split_phases: batching without the "
+                    "construct-then-operate pieces",
             "saturation_GB/s": sat, "saturation_runs_GB/s": s.get("saturation_runs_GB/s"),
             "saturation_frac_measured": s.get("saturation_frac_measured"),
             "saturation_dram_GB/s": s.get("saturation_dram_GB/s"),
@@ -514,20 +515,27 @@ def served_section(sx, torch, t, stream, args, rank):
                        f"moved per request", "saturation_GB/s": {}, "runs": []}
     zero = [0.0] * len(work)
     # untimed warm-up of both modes (the first server of a process starts cold), then each mode
-    # at saturation twice, alternating; the better run of each is its saturation throughput
+    # at saturation twice, alternating; the better run of each is its saturation throughput.
+    # Beside them continuous batching with split_phases (inputs constructed in one piece, the
+    # operation in a later one, reading them back from DRAM): what batching alone gives, without
+    # the construct-then-operate pieces
     for mode, _ in modes:
         serve_run(sx, t, work[:200], zero[:200], budget, mode)
-    sat = {name: [] for _, name in modes}
+    sat_modes = ((sx.SX_SERVE_CONTINUOUS, "continuous", {}), (sx.SX_SERVE_CONTINUOUS, "continuous_split_phases",
+                                                          {"split_phases": 1}), (sx.SX_SERVE_FIFO, "fifo", {}))
+    sat = {name: [] for _, name, _ in sat_modes}
     for _ in range(2):
-        for mode, name in modes:
-            _, stats, span = serve_run(sx, t, work, zero, budget, mode)
+        for mode, name, kw in sat_modes:
+            _, stats, span = serve_run(sx, t, work, zero, budget, mode, kw)
             sat[name].append(stats["bytes_moved"] / span / 1e9)
     for name, runs in sat.items():
         out["saturation_GB/s"][name] = round(max(runs), 1)
         out.setdefault("saturation_runs_GB/s", {})[name] = [round(v, 1) for v in runs]
         out.setdefault("saturation_frac_measured", {})[name] = round(max(runs) / _measured_peaks()[0], 4)
-        # the DRAM traffic each mode has to move for the same work, at that rate
-        out.setdefault("saturation_dram_GB/s", {})[name] = round(max(runs) * dram[name] / sum(nbytes), 1)
+        # the DRAM traffic each mode has to move for the same work, at that rate (split phases: short
+        # requests run fused and the others read their inputs back, between the two)
+        if name in dram:
+            out.setdefault("saturation_dram_GB/s", {})[name] = round(max(runs) * dram[name] / sum(nbytes), 1)
     out["dram_bytes_per_stream_byte"] = {k: round(v / sum(nbytes), 4) for k, v in dram.items()}
     capacity = out["saturation_GB/s"]["fifo"] * 1e9
     out["capacity_from"] = "per-call FIFO throughput at saturation"
