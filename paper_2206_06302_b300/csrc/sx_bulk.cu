@@ -398,14 +398,32 @@ k_stream_tma(const T *x, const T *y, T *out, uint64_t n, uint64_t head, uint64_t
             const uint32_t nv = tile_len(j) / 16;
             const uint32_t sx0 = smem_addr(slot_x(s));
             const uint32_t sy0 = HAS_Y ? smem_addr(slot_y(s)) : 0u;
-            for (uint32_t v = ctid; v < nv; v += ncons) {
+            // two 16-byte vectors per thread and step (both loaded before either is computed, so
+            // each thread waits on shared memory once per two vectors), a lone last one on its own
+            auto ld2 = [](uint32_t a, uint64_t &w0, uint64_t &w1) {
+                asm volatile("ld.shared.v2.u64 {%0,%1}, [%2];" : "=l"(w0), "=l"(w1) : "r"(a));
+            };
+            auto st2 = [](uint32_t a, uint64_t w0, uint64_t w1) {
+                asm volatile("st.shared.v2.u64 [%0], {%1,%2};" ::"r"(a), "l"(w0), "l"(w1) : "memory");
+            };
+            uint32_t v = ctid;
+            for (; v + ncons < nv; v += 2 * ncons) {
+                const uint32_t u = v + ncons;
+                uint64_t a0, a1, c0, c1, b0 = 0, b1 = 0, d0 = 0, d1 = 0;
+                ld2(sx0 + 16 * v, a0, a1);
+                ld2(sx0 + 16 * u, c0, c1);
+                if constexpr (HAS_Y) {
+                    ld2(sy0 + 16 * v, b0, b1);
+                    ld2(sy0 + 16 * u, d0, d1);
+                }
+                st2(sx0 + 16 * v, op_word<OP, T, MM>(a0, b0, q, 0), op_word<OP, T, MM>(a1, b1, q, 1));
+                st2(sx0 + 16 * u, op_word<OP, T, MM>(c0, d0, q, 0), op_word<OP, T, MM>(c1, d1, q, 1));
+            }
+            if (v < nv) {
                 uint64_t a0, a1, b0 = 0, b1 = 0;
-                asm volatile("ld.shared.v2.u64 {%0,%1}, [%2];" : "=l"(a0), "=l"(a1) : "r"(sx0 + 16 * v));
-                if constexpr (HAS_Y)
-                    asm volatile("ld.shared.v2.u64 {%0,%1}, [%2];" : "=l"(b0), "=l"(b1) : "r"(sy0 + 16 * v));
-                const uint64_t r0 = op_word<OP, T, MM>(a0, b0, q, 0);
-                const uint64_t r1 = op_word<OP, T, MM>(a1, b1, q, 1);
-                asm volatile("st.shared.v2.u64 [%0], {%1,%2};" ::"r"(sx0 + 16 * v), "l"(r0), "l"(r1) : "memory");
+                ld2(sx0 + 16 * v, a0, a1);
+                if constexpr (HAS_Y) ld2(sy0 + 16 * v, b0, b1);
+                st2(sx0 + 16 * v, op_word<OP, T, MM>(a0, b0, q, 0), op_word<OP, T, MM>(a1, b1, q, 1));
             }
             fence_async_smem();  // this thread's results are visible to the bulk store
             __syncwarp();

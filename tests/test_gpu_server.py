@@ -138,6 +138,25 @@ def test_fused_requests_with_a_general_range(target):
         sx.sx_server_destroy(s)
 
 
+@pytest.mark.parametrize("split", [0, 1])
+def test_ranged_pieces_with_a_general_range(target, split):
+    """Long requests over a general input range [lo, hi), both types and all four ops, cut into
+    many pieces (1 MiB steps, 16 KiB tiles) that share steps with each other: every piece builds
+    its range of the inputs at its generator indices and applies the operation to it (or, with
+    split_phases, in two phases).  Inputs and results are the oracle's bit for bit."""
+    reqs = [dict(op=op, dtype=dt, n=n, q=q, seed_x=31 + 7 * k, seed_y=32 + 7 * k, lo=-3.0, hi=5.5)
+            for k, (op, dt, n, q) in enumerate(
+                (op, dt, n, q) for op in (sx.SX_OP_COPY, sx.SX_OP_SCALE, sx.SX_OP_ADD, sx.SX_OP_TRIAD)
+                for dt in (sx.SX_F64, sx.SX_F32) for n, q in ((100003, 3.0), (262147, -0.7)))]
+    s = sx.sx_server_create(target, budget_bytes=1 << 30, chunk_bytes=1 << 20, tile_bytes=16384,
+                            split_phases=split)
+    ids = [sx.sx_server_submit(s, **r) for r in reqs]
+    _check_all(s, ids, reqs, f"ranged, split_phases={split}")
+    st = sx.sx_server_stats_get(s)
+    assert st["completed"] == len(reqs) and st["steps"] > len(reqs) // 2, st
+    sx.sx_server_destroy(s)
+
+
 def test_replayed_poisson_stream(target):
     reqs = _requests(150, seed=5)
     arr = si.poisson_requests(5, 150, rate_per_s=20000.0)
