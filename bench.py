@@ -1110,10 +1110,10 @@ def run_ours(args):
         el = time.perf_counter() - t0
         e2e_gbs, el_ms = job_throughput(dist, el * 1e3, step_bytes, args.e2e_steps, world, "cuda", scaling)
         e2e = {"value": round(e2e_gbs, 2), "unit": "GB/s",
-               "h2d_bytes_per_step": 3 * n_local * es, "d2h_bytes_per_step": 3 * n_local * es,
+               "h2d_bytes_per_step": n_local * es, "d2h_bytes_per_step": 3 * n_local * es,
                "steps": args.e2e_steps,
-               "what": "sx_stream_host: h2d a,b,c + one pass + d2h a,b,c from pinned host memory, "
-                       "pipelined in 32 MiB chunks over 3 streams; host clock"}
+               "what": "sx_stream_host: h2d a (a pass writes b and c before reading them) + one pass + "
+                       "d2h a,b,c from pinned host memory, pipelined in 32 MiB chunks over 3 streams; host clock"}
         for d in dev:
             sx.sx_free(d)
         sx.sx_executor_destroy(esync)

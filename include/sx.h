@@ -282,8 +282,10 @@ int sx_stream_iter(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double
 /* The same `iters` passes computed by one kernel that reads a once and writes a, b, c once;
  * bit-identical results (each element's chain of roundings is the same). */
 int sx_stream_fused(sx_executor *e, sx_array *a, sx_array *b, sx_array *c, double q, int iters);
-/* End to end from host memory: copy a, b, c (n elements, pinned or pageable host memory) to
- * the target's arrays, run `iters` passes of sx_stream_iter, copy the three arrays back.
+/* End to end from host memory: copy a (n elements, pinned or pageable host memory) to the
+ * target's array, run `iters` passes of sx_stream_iter, copy a, b and c back.  A pass writes c
+ * (Copy) and b (Scale) before it reads them, so their start values are not copied in unless
+ * iters is 0 (then all three make the round trip).
  * The work goes in 32 MiB chunks over three internal streams (every element's passes are
  * independent), so copies in both directions and the kernels overlap; with pinned host memory
  * the two link directions run at once.  Same bits as the unchunked sequence.  Returns after the

@@ -733,8 +733,12 @@ int sx_stream_host(sx_executor *e, void *ha, void *hb, void *hc, sx_array *a, sx
         const size_t ob = off * es, mb = m * es;
         cudaStream_t s = t->pipe[k % sx_target::kPipe];
         SX_CUDA(cudaMemcpyAsync(pa + ob, qa + ob, mb, cudaMemcpyHostToDevice, s));
-        SX_CUDA(cudaMemcpyAsync(pb + ob, qb + ob, mb, cudaMemcpyHostToDevice, s));
-        SX_CUDA(cudaMemcpyAsync(pc + ob, qc + ob, mb, cudaMemcpyHostToDevice, s));
+        if (iters == 0) {
+            // a pass writes c (Copy) and b (Scale) before it reads them, so their start values
+            // only matter when no pass runs
+            SX_CUDA(cudaMemcpyAsync(pb + ob, qb + ob, mb, cudaMemcpyHostToDevice, s));
+            SX_CUDA(cudaMemcpyAsync(pc + ob, qc + ob, mb, cudaMemcpyHostToDevice, s));
+        }
         const int ops[4] = {SX_OP_COPY, SX_OP_SCALE, SX_OP_ADD, SX_OP_TRIAD};
         for (int it = 0; it < iters; ++it) {
             for (int op : ops) {

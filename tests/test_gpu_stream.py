@@ -564,6 +564,32 @@ def test_stream_host_end_to_end(target, executor):
             sx.sx_free(h)
 
 
+def test_stream_host_reads_only_a(target, executor):
+    """A pass writes c and b before reading them, so sx_stream_host copies only a to the device:
+    host b and c holding NaNs (and device b, c holding other values) give the oracle's results of
+    the seeded arrays; with zero passes all three arrays make the round trip unchanged."""
+    n = (3 << 20) + 77
+    for dt in (np.float64, np.float32):
+        a, b, c = si.stream_arrays(n, dt, base_seed=24)
+        ha, hb, hc = a.copy(), np.full(n, np.nan, dt), np.full(n, np.nan, dt)
+        da, db, dc = (empty(target, dt, n) for _ in range(3))
+        sx.sx_bulk_construct(db, -5.0)
+        sx.sx_bulk_construct(dc, 9.0)
+        sx.sx_stream_host(executor, ha.ctypes.data, hb.ctypes.data, hc.ctypes.data, da, db, dc, 3.0, 2)
+        oracle.stream(a, b, c, 3.0, 2)
+        for h, w, name in ((ha, a, "a"), (hb, b, "b"), (hc, c, "c")):
+            assert_bitwise(h, w, f"{dt.__name__} {name}")
+        x, y, z = si.stream_arrays(n, dt, base_seed=25)
+        hx, hy, hz = x.copy(), y.copy(), z.copy()
+        sx.sx_stream_host(executor, hx.ctypes.data, hy.ctypes.data, hz.ctypes.data, da, db, dc, 3.0, 0)
+        for h, w, name in ((hx, x, "a"), (hy, y, "b"), (hz, z, "c")):
+            assert_bitwise(h, w, f"{dt.__name__} round trip {name}")
+        for d, w in ((da, x), (db, y), (dc, z)):
+            assert_bitwise(to_host(d), w, "device copy after the round trip")
+        for h in (da, db, dc):
+            sx.sx_free(h)
+
+
 def _random_doubles(n, seed):
     """Bit patterns spread over every binary64 exponent (zeros, subnormals, normals near the
     overflow threshold, infinities and NaNs included)."""
