@@ -162,10 +162,7 @@ __device__ __forceinline__ void run_tile(const DevItem &it, uint64_t start, uint
 // operation's additions (and half of its products) already occupy the FP64 pipe, so fewer of
 // these pieces' values go there than in plain construction (5 of 8): on the served workload 0 or
 // 1 of 4 moved 8.5-8.8 TB/s, 2 of 4 8.2-8.8, 3 of 4 7.7-8.1, 4 of 4 7.2-7.5.
-#ifndef SX_FUSED_PM1_SUB
-#define SX_FUSED_PM1_SUB 1
-#endif
-constexpr int kFusedPm1Sub = SX_FUSED_PM1_SUB;
+constexpr int kFusedPm1Sub = 1;
 
 template <class T, bool PM1>
 __device__ __forceinline__ T fused_input(uint64_t z, T lo, T span, int j) {

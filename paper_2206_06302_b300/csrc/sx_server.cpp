@@ -280,7 +280,7 @@ int launch_step(sx_server *s, bool *launched) {
     const uint64_t budget = (uint64_t)(uint32_t)s->cfg.chunk_bytes;
     std::vector<sched::Want> w;
     std::vector<Request *> by_key;
-    std::vector<uint8_t> whole;  // short and not started: planned with the bytes of both phases
+    std::vector<uint8_t> fused;  // construct-then-operate pieces: planned with the bytes of both phases
     const bool split = s->cfg.split_phases != 0;
     for (Request *q : s->active) {
         if (q->phase >= 2) continue;
@@ -288,12 +288,12 @@ int launch_step(sx_server *s, bool *launched) {
         // fused: every piece constructs its range of the inputs and applies the operation to it;
         // split: short requests (whole work at most a quarter of the budget) as one such piece,
         // the others in two phases
-        const bool fused = !split || (q->phase == 0 && q->next == 0 && (uint64_t)q->r.n * (p0 + p1) <= budget / 4);
-        const uint64_t later = q->phase == 0 && !fused ? (uint64_t)q->r.n * p1 : 0;
-        const uint64_t per = fused ? p0 + p1 : phase_bytes_per_elem(*q, q->phase);
+        const bool cto = !split || (q->phase == 0 && q->next == 0 && (uint64_t)q->r.n * (p0 + p1) <= budget / 4);
+        const uint64_t later = q->phase == 0 && !cto ? (uint64_t)q->r.n * p1 : 0;
+        const uint64_t per = cto ? p0 + p1 : phase_bytes_per_elem(*q, q->phase);
         w.push_back({by_key.size(), q->admit_seq, per, q->r.n - q->next, later});
         by_key.push_back(q);
-        whole.push_back(fused ? 1 : 0);
+        fused.push_back(cto ? 1 : 0);
     }
     if (w.empty()) return SX_OK;
     // elements of each request's current phase in this step, in the policy's order (sx_sched.h)
@@ -313,7 +313,7 @@ int launch_step(sx_server *s, bool *launched) {
         const uint64_t lo = q->next, hi = lo + elems;
         const sx_request &r = q->r;
         const size_t es = dtype_size(r.dtype);
-        if (whole[w[i].key] && (!split || elems == r.n)) {
+        if (fused[w[i].key] && (!split || elems == r.n)) {
             // construct x (and y) over [lo, hi), then the operation on that range, tile by tile
             StepItem si;
             si.item.op = r.op;
