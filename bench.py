@@ -197,8 +197,12 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded SplitMix64 uniform [-1,1)",
-        "config": {"workload": f"STREAM FP64 pass (copy,scale,add,triad), q=3, bounded sample "
-                               f"n={n} per array of the n=2^27 workload", "n": n},
+        "config": {"workload": f"STREAM F64 n=2^{args.n.bit_length() - 1} per array "
+                               f"({args.n * 8 / 2 ** 30:g} GiB each), q={Q:g}; step = one pass "
+                               "copy,scale,add,triad (4 launches)",
+                   "n": args.n, "sample_n": n,
+                   "sample": f"each step is the oracle's pass over n={n} per array, a bounded sample "
+                             "of the workload; GB/s counts the sample's STREAM bytes"},
         "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"n={n} FP64 per array, {args.steps} passes", "cpu": _cpu_model()},
         "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
