@@ -284,7 +284,14 @@ def batched_section(sx, torch, t, stream, args, rank):
     launches' outputs are compared bit for bit on 8 instances (parity with the oracle is the
     tests' part), and those instances' inputs against the seeded generator."""
     import stream_inputs as si
-    inst = si.batched_instances(si.BASE_SEED + rank, args.batch_count)
+    _, world, _ = _rank_env()
+    if args.shard:
+        # instances assigned whole to ranks: this rank's contiguous block of the one workload,
+        # each instance seeded by its index in the whole list
+        first, count = shard_block(sx, args.batch_count, world, rank)
+        inst = si.batched_instances(si.BASE_SEED, args.batch_count)[first:first + count]
+    else:
+        first, inst = 0, si.batched_instances(si.BASE_SEED + rank, args.batch_count)
     offs, total = [], 0
     for _, n in inst:
         r = []
@@ -299,7 +306,7 @@ def batched_section(sx, torch, t, stream, args, rank):
     for k, (_, n) in enumerate(inst):
         for j in (0, 1):
             seeds.append(sx.sx_batch_item(op=sx.SX_OP_SEED, dtype=sx.SX_F64, n=n, out=base + offs[k][j],
-                                          q=-1.0, q2=1.0, seed=si.array_seed(si.BASE_SEED, j, k)))
+                                          q=-1.0, q2=1.0, seed=si.array_seed(si.BASE_SEED, j, first + k)))
     sb = sx.sx_batch_create(t, seeds)
     sx.sx_batch_launch(sb)
     sx.sx_target_synchronize(t)
@@ -384,12 +391,14 @@ def batched_section(sx, torch, t, stream, args, rank):
     after_noalloc = snapshot(2)
     same = all(np.array_equal(g, p) for g, p in zip(after_graph, after_percall))
     same_noalloc = all(np.array_equal(g, p) for g, p in zip(after_graph, after_noalloc))
-    inputs_ok = all(np.array_equal(h, si.uniform(si.array_seed(si.BASE_SEED, 0, k), inst[k][1], np.float64)
+    inputs_ok = all(np.array_equal(h, si.uniform(si.array_seed(si.BASE_SEED, 0, first + k), inst[k][1], np.float64)
                                    .view(np.uint64)) for k, h in zip(spot, snapshot(0)))
     sx.sx_batch_destroy(b)
     sx.sx_free(buf)
     gm, pm = g_ms[len(g_ms) // 2], p_ms[len(p_ms) // 2]
     return {
+        "share": (f"instances [{first}, {first + len(inst)}) of {args.batch_count}, assigned whole to this rank"
+                  if args.shard else "all instances"),
         "workload": f"{len(items)} FP64 triad/add instances, n log-uniform in [2^10, 2^22] "
                     f"(seeded), {nbytes / 1e9:.1f} GB moved per launch",
         "tuned": cfg, "tiles": tiles,
@@ -475,13 +484,19 @@ def serve_run(sx, t, work, times, budget_bytes, mode, server_kw=None):
     return lat, stats, (t1 - t0) if t1 is not None else float("nan")
 
 
-def served_workload(sx, seed, count, dram=None):
-    """The served requests (sx_request list), their element counts and STREAM byte counts.  If
-    `dram` is a dict, it receives the workload's total DRAM bytes under each mode: "continuous"
-    (every piece stores x, y and out and reads nothing back) and "fifo" (the operation reads the
-    inputs back from DRAM)."""
+def shard_requests(reqs, world, rank):
+    """A served request stream dealt out to `world` servers in turn (request k to rank k mod
+    world), each keeping its requests' arrival times: every rank sees 1/world of the rate."""
+    return [r for k, r in enumerate(reqs) if k % world == rank]
+
+
+def served_workload(sx, seed, count, dram=None, world=1, rank=0):
+    """The served requests (sx_request list), their element counts and STREAM byte counts (with
+    world > 1: rank's share, shard_requests).  If `dram` is a dict, it receives the workload's
+    total DRAM bytes under each mode: "continuous" (every piece stores x, y and out and reads
+    nothing back) and "fifo" (the operation reads the inputs back from DRAM)."""
     import stream_inputs as si
-    reqs = si.poisson_requests(seed, count, rate_per_s=1.0)
+    reqs = shard_requests(si.poisson_requests(seed, count, rate_per_s=1.0), world, rank)
     ops = {"copy": sx.SX_OP_COPY, "scale": sx.SX_OP_SCALE, "add": sx.SX_OP_ADD, "triad": sx.SX_OP_TRIAD}
     dts = {"f64": (sx.SX_F64, 8), "f32": (sx.SX_F32, 4)}
     work, nbytes = [], []
@@ -510,13 +525,18 @@ def served_section(sx, torch, t, stream, args, rank):
     by the server), the p99 of the shorter half of the requests, and throughput."""
     import stream_inputs as si
     dram = {}
-    reqs, work, nbytes = served_workload(sx, si.BASE_SEED + 7 + rank, args.serve_count, dram)
+    _, world, _ = _rank_env()
+    if args.shard:  # one request stream dealt out to the ranks
+        reqs, work, nbytes = served_workload(sx, si.BASE_SEED + 7, args.serve_count, dram, world, rank)
+    else:
+        reqs, work, nbytes = served_workload(sx, si.BASE_SEED + 7 + rank, args.serve_count, dram)
     mean_bytes = sum(nbytes) / len(nbytes)
     budget = int(args.serve_budget_gb * 1e9)
     median_n = sorted(r["n"] for r in reqs)[len(reqs) // 2]
     short = [k for k, r in enumerate(reqs) if r["n"] <= median_n]
     modes = ((sx.SX_SERVE_CONTINUOUS, "continuous"), (sx.SX_SERVE_FIFO, "fifo"))
-    out = {"workload": f"{len(reqs)} Poisson requests, ops uniform over copy/scale/add/triad, "
+    out = {"share": (f"requests k with k mod {world} = {rank} of {args.serve_count}" if args.shard else "all requests"),
+           "workload": f"{len(reqs)} Poisson requests, ops uniform over copy/scale/add/triad, "
                        f"FP64/FP32 50/50, n log-uniform in [2^12, 2^28], inputs constructed on "
                        f"device, {args.serve_budget_gb:g} GB arena, mean {mean_bytes / 1e6:.1f} MB "
                        f"moved per request", "saturation_GB/s": {}, "runs": []}

@@ -46,3 +46,32 @@ def test_served_workload_byte_accounting():
     written = sum(r["n"] * (8 if r["dtype"] == "f64" else 4) * (3 if r["op"] in ("add", "triad") else 2)
                   for r in reqs)
     assert dram["continuous"] == written < dram["fifo"]
+
+
+def test_shard_requests_deal_every_request_once():
+    import stream_inputs as si
+    reqs = si.poisson_requests(5, 1001, rate_per_s=1.0)
+    for world in (1, 2, 3, 8):
+        parts = [bench.shard_requests(reqs, world, r) for r in range(world)]
+        assert sum(len(p) for p in parts) == len(reqs)
+        seen = sorted((r["t"], r["seed"]) for p in parts for r in p)
+        assert seen == sorted((r["t"], r["seed"]) for r in reqs)
+        assert max(len(p) for p in parts) - min(len(p) for p in parts) <= 1
+    import paper_2206_06302_b300 as sx
+    full = bench.served_workload(sx, 5, 1001)[2]
+    halves = [bench.served_workload(sx, 5, 1001, None, 2, r)[2] for r in (0, 1)]
+    assert sorted(full) == sorted(halves[0] + halves[1])
+
+
+def test_batched_instances_assigned_whole_in_blocks():
+    """--shard gives each rank a contiguous block of the one batched workload (sx_block_partition
+    over the instance count): the blocks put together are the whole list, in order."""
+    import paper_2206_06302_b300 as sx
+    import stream_inputs as si
+    inst = si.batched_instances(si.BASE_SEED, 4096)
+    for world in (1, 2, 3, 8):
+        parts = []
+        for r in range(world):
+            first, count = bench.shard_block(sx, len(inst), world, r)
+            parts.extend(inst[first:first + count])
+        assert parts == inst
