@@ -2,9 +2,10 @@
  *
  * a = 1, b = 2, c = 0 (bulk construction on the device, Section 3.2), q = 3, ten passes of
  * Listing 4 (sx_stream_iter), then the arrays are copied back and checked against the exact
- * values a = 15^10, b = 3 * 15^9, c = 4 * 15^9 (exact in binary64).  Exit status: 0 when the
- * check passes, 1 on a wrong value or a failed call, 2 when no device is present (the message
- * of the failing call is printed). */
+ * values a = 15^10, b = 3 * 15^9, c = 4 * 15^9 (exact in binary64).  Before any device call it
+ * checks the block partition of Section 4.1 (host arithmetic): the blocks of n elements over
+ * 1..8 parts tile [0, n) in order.  Exit status: 0 when the checks pass, 1 on a wrong value or a
+ * failed call, 2 when no device is present (the message of the failing call is printed). */
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -17,7 +18,28 @@ static int check(int status, const char *what) {
     return status;
 }
 
+static int check_partition(void) {
+    const uint64_t sizes[4] = {0, 7, 1000003, ((uint64_t)1 << 33) + 5};
+    for (int i = 0; i < 4; ++i)
+        for (int parts = 1; parts <= 8; ++parts) {
+            uint64_t at = 0;
+            for (int part = 0; part < parts; ++part) {
+                uint64_t off = 0, cnt = 0;
+                if (check(sx_block_partition(sizes[i], parts, part, &off, &cnt), "sx_block_partition")) return 1;
+                if (off != at) {
+                    fprintf(stderr, "block %d of %d: offset %llu, want %llu\n", part, parts,
+                            (unsigned long long)off, (unsigned long long)at);
+                    return 1;
+                }
+                at += cnt;
+            }
+            if (at != sizes[i]) return 1;
+        }
+    return 0;
+}
+
 int main(void) {
+    if (check_partition()) return 1;
     int count = 0;
     if (sx_target_count(&count) != SX_OK || count < 1) {
         fprintf(stderr, "no device: %s\n", sx_last_error());
