@@ -438,9 +438,10 @@ typedef struct sx_server_cfg {
                                 (programmatic dependent launch; pieces that need the previous
                                 step's data wait for it); 1 = steps run strictly one after another */
     int32_t split_phases;    /* CONTINUOUS: 0 = every piece constructs its range of the inputs and
-                                then applies the operation to it, tile by tile (the inputs are read
-                                back from L2); 1 = requests over a quarter of the step budget run
-                                in two phases, inputs first, the operation in a later piece       */
+                                applies the operation to it in the same pass (each element's
+                                inputs are computed, stored and used from registers); 1 = requests
+                                over a quarter of the step budget run in two phases, inputs first,
+                                the operation in a later piece reading them back              */
 } sx_server_cfg;
 
 /* CONTINUOUS sharing policies.  SRPT (default): shortest remaining work first; each request in

@@ -207,10 +207,10 @@ void step_slot_free(StepSlot &s);
 size_t step_tile_count(const sx_batch_item *items, size_t count, int tile_bytes);
 // One piece of a serving step: a batch item and how the step treats it.
 //   kStepDependent        waits for the previous step to complete before its first tile
-//   kStepConstructThenOp  a whole short request: each tile constructs its range of x (and y) from
-//                         item.seed (and seed2) over [item.q2, hi), then applies item.op (scalar
-//                         item.q) to it, reading the inputs back; item.index_base is the generator
-//                         index of element 0
+//   kStepConstructThenOp  a range of a request: each element's x (and y) is computed from item.seed
+//                         (and seed2) over [item.q2, hi) in registers and stored, and item.op
+//                         (scalar item.q) is applied to those values and stored; item.index_base is
+//                         the generator index of element 0
 // fin_word: 1 + index of the completion word the piece reports to when its last tile is done (0:
 // none).
 struct StepItem {

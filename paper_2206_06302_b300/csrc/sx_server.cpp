@@ -10,10 +10,10 @@
 // CONTINUOUS mode batches requests continuously.  A step is one launch of the batched kernel
 // (sx_batch.cu) over a list of pieces, passed in the launch's parameters: for each active
 // request a range of its elements.  By default every piece is a construct-then-operate piece:
-// each tile builds its range of the inputs from their seeds and then applies the operation to
-// it, reading the inputs back while they are still in L2, so the integer-bound construction of
-// one block overlaps the memory-bound operations of others on the same SM, and the operation's
-// input reads do not go to DRAM.  (With split_phases, as before, phase 0 constructs x and y and
+// for each element the inputs are computed from their seeds in registers and stored, and the
+// operation is applied to those register values and stored, so the operation's inputs are never
+// read back from memory and the integer-bound construction of some blocks overlaps the stores
+// of others on the same SM.  (With split_phases, as before, phase 0 constructs x and y and
 // phase 1 runs the operation in a later piece; only short requests are fused.)  The step's byte
 // budget goes by policy, shortest remaining work first by default, so short requests finish in
 // the first step that takes them while long ones advance in the rest.  Up to steps_in_flight
@@ -726,9 +726,9 @@ int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out) {
     if (c.chunk_bytes < (1 << 20)) return fail(SX_ERR_INVALID, "chunk_bytes %d below 1 MiB", c.chunk_bytes);
     if (c.steps_in_flight < 1 || c.steps_in_flight > 8) return fail(SX_ERR_INVALID, "steps_in_flight %d", c.steps_in_flight);
     // default step-kernel shape, measured on the served workload with construct-then-operate
-    // pieces: four blocks of 256 threads per SM (the kernel's 63 registers allow 1024 threads),
-    // so that blocks constructing (integer-bound) and blocks operating (memory-bound) share each
-    // SM, and 128 KiB tiles, whose inputs are still in L2 when the tile's operation reads them
+    // pieces: four blocks of 256 threads per SM (the kernel's 61 registers allow 1024 threads),
+    // so that several blocks at different points of their tiles share each SM, and 128 KiB tiles
+    // (32 KiB tiles and 1024-thread blocks were the slowest of the shapes measured)
     sx_batch_cfg k{};
     k.chunk_bytes = c.tile_bytes ? c.tile_bytes : 128 * 1024;
     k.threads = c.threads ? c.threads : 256;
