@@ -536,9 +536,10 @@ struct StepParams {
     uint64_t seq;
     unsigned long long *done;
     unsigned int *counter;
-    // per-piece completion words (pieces with pad bits 8..): the block that finishes a piece's
-    // last tile sets fin_host[w] (host-mapped) to 1; fin_count[w] counts its finished tiles and is
-    // left at zero for the word's next use
+    // per-piece completion words (pieces with pad bits 8..): the warp that finishes the piece's
+    // last part (ntiles x warps per block parts, one per warp and tile) sets fin_host[w]
+    // (host-mapped) to 1; fin_count[w] counts the finished parts and is left at zero for the
+    // word's next use
     unsigned long long *fin_host;
     unsigned int *fin_count;
     uint32_t prefix[kStepMaxItems + 1];

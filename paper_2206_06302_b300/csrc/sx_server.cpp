@@ -22,7 +22,7 @@
 // complete waits for it on the device.  The thread builds the next step while the GPU runs the
 // previous ones, admits arrivals between steps, and marks a request DONE when the step holding
 // its last piece has completed.  A request that a step takes whole, in one piece, reports its
-// own completion: the block that finishes the piece's last tile sets a host-mapped word, and the
+// own completion: the warp that finishes the piece's last part sets a host-mapped word, and the
 // request is DONE as soon as the thread sees it, without waiting for the rest of the step.
 //
 // FIFO mode is the per-call baseline: each admitted request is enqueued at once as its own
