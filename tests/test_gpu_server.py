@@ -157,6 +157,32 @@ def test_ranged_pieces_with_a_general_range(target, split):
     sx.sx_server_destroy(s)
 
 
+def test_completion_words_are_recycled(target):
+    """More whole-request pieces over a server's life than it has completion words (4096): every
+    word goes back to the pool when its request completes, so 6000 short requests (submitted in
+    waves, so that many are in flight at once) all complete, each with the oracle's result on a
+    sample, and the pool never runs dry for good."""
+    s = sx.sx_server_create(target, budget_bytes=1 << 30, chunk_bytes=1 << 20)
+    total, wave = 6000, 750
+    reqs = [dict(op=[sx.SX_OP_COPY, sx.SX_OP_SCALE, sx.SX_OP_ADD, sx.SX_OP_TRIAD][k % 4],
+                 dtype=sx.SX_F64 if k % 2 else sx.SX_F32, n=64 + (k * 37) % 900, q=-1.5,
+                 seed_x=5000 + k, seed_y=9000 + k, lo=-1.0, hi=1.0) for k in range(total)]
+    for first in range(0, total, wave):
+        batch = reqs[first:first + wave]
+        ids = [sx.sx_server_submit(s, **r) for r in batch]
+        checked = [(rid, r) for k, (rid, r) in enumerate(zip(ids, batch)) if k % 50 == 0]
+        _check_all(s, [i for i, _ in checked], [r for _, r in checked], f"wave {first // wave}")
+        for k, rid in enumerate(ids):
+            if k % 50:
+                st = sx.sx_server_wait(s, rid, 60000)
+                assert st["state"] == sx.SX_REQ_DONE, st
+                sx.sx_server_release(s, rid)
+    st = sx.sx_server_stats_get(s)
+    assert st["completed"] == total and st["fused"] == total, st
+    assert 0 < st["early_done"] <= total and st["arena_used"] == 0, st
+    sx.sx_server_destroy(s)
+
+
 def test_replayed_poisson_stream(target):
     reqs = _requests(150, seed=5)
     arr = si.poisson_requests(5, 150, rate_per_s=20000.0)
