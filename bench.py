@@ -99,8 +99,79 @@ def _kernel_source_sha():
     return h.hexdigest()
 
 
+# NVML clock-event reason bits (nvmlClocksEventReason*) the bench reports by name
+NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+
+def clock_summary(samples, window, max_mhz):
+    """Summary of (time, SM MHz, reason bits) samples: those inside `window` (start, end), or all
+    if none falls inside; the median SM clock and every reason seen active."""
+    lo, hi = window
+    inside = [x for x in samples if lo is not None and hi is not None and lo <= x[0] <= hi] or list(samples)
+    if not inside:
+        return None
+    reasons = sorted({name for _, _, bits in inside for bit, name in NVML_REASONS.items() if bits & bit})
+    return {"sm_mhz": statistics.median(m for _, m, _ in inside), "sm_max_mhz": max_mhz,
+            "reasons": reasons, "samples": len(inside)}
+
+
+class NvmlReader:
+    """Reads (never sets) a GPU's SM clock, maximum SM clock and clock-event reasons through the
+    driver's NVML library (libnvidia-ml.so.1) with ctypes.  The GPU is found by the UUID CUDA
+    reports for `device` (NVML's indices need not follow CUDA's), else by index."""
+
+    def __init__(self, lib, handle, reasons_fn):
+        self.lib, self.h, self._reasons = lib, handle, reasons_fn
+
+    @classmethod
+    def open(cls, device):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            found = False
+            try:
+                import torch
+                uuid = "GPU-" + str(torch.cuda.get_device_properties(device).uuid)
+                found = lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) == 0
+            except Exception:  # noqa: BLE001 (no UUID from CUDA: by index)
+                found = False
+            if not found and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device), ctypes.byref(h)) != 0:
+                return None
+            fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            return cls(lib, h, fn)
+        except (OSError, AttributeError):
+            return None
+
+    def _clock(self, getter):
+        import ctypes
+        v = ctypes.c_uint(0)
+        if getter(self.h, ctypes.c_int(1), ctypes.byref(v)) != 0:  # 1: NVML_CLOCK_SM
+            raise OSError("NVML clock query failed")
+        return v.value
+
+    def sm_mhz(self):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo)
+
+    def sm_max_mhz(self):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo)
+
+    def reasons(self):
+        import ctypes
+        v = ctypes.c_ulonglong(0)
+        if self._reasons(self.h, ctypes.byref(v)) != 0:
+            raise OSError("NVML reasons query failed")
+        return v.value
+
+
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    """SM clocks and throttle reasons during the timed region: NVML read every 2 ms by a thread
+    (the samples between mark_start and mark_stop are summarised), and nvidia-smi every 100 ms
+    beside it."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -109,8 +180,25 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.path = None
+        self.nvml_samples, self.window, self.nvml_max = [], [None, None], None
+        self._stop = False
+        self._thread = None
+
+    def _poll_nvml(self, nvml):
+        while not self._stop:
+            try:
+                self.nvml_samples.append((time.perf_counter(), nvml.sm_mhz(), nvml.reasons()))
+            except OSError:  # a sample that fails is skipped
+                pass
+            time.sleep(0.002)
 
     def __enter__(self):
+        nvml = NvmlReader.open(self.device)
+        if nvml is not None:
+            import threading
+            self.nvml_max = nvml.sm_max_mhz()
+            self._thread = threading.Thread(target=self._poll_nvml, args=(nvml,), daemon=True)
+            self._thread.start()
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
@@ -123,7 +211,16 @@ class ClockSampler:
             self.proc = None
         return self
 
+    def mark_start(self):
+        self.window[0] = time.perf_counter()
+
+    def mark_stop(self):
+        self.window[1] = time.perf_counter()
+
     def __exit__(self, *exc):
+        self._stop = True
+        if self._thread is not None:
+            self._thread.join(timeout=1)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -131,7 +228,7 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    def smi_summary(self):
         if self.proc is None or not self.path or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, smax, power, reasons = [], [], [], set()
@@ -155,6 +252,19 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
                 "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+    def summary(self):
+        """NVML's summary of the timed region (with nvidia-smi's beside it), or nvidia-smi's alone."""
+        smi = self.smi_summary()
+        nv = clock_summary(self.nvml_samples, self.window, self.nvml_max) if self.nvml_samples else None
+        if nv is None:
+            return smi
+        nv["source"] = "NVML every 2 ms between the start and the end of the timed passes"
+        if smi.get("reasons"):
+            nv["reasons"] = sorted(set(nv["reasons"]) | {r for r in smi["reasons"] if "unavailable" not in r
+                                                        and r != "no samples"})
+        nv["smi"] = smi
+        return nv
 
 
 # ----------------------------------------------------------------------------------------------
@@ -1061,9 +1171,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
+        clocks.mark_start()
         for s in range(args.steps):
             one_pass(events[s])
         torch.cuda.synchronize()
+        clocks.mark_stop()
     if dist:
         dist.barrier()
     sx.sx_target_synchronize(t)  # surfaces any device-side error word

@@ -75,3 +75,14 @@ def test_batched_instances_assigned_whole_in_blocks():
             first, count = bench.shard_block(sx, len(inst), world, r)
             parts.extend(inst[first:first + count])
         assert parts == inst
+
+
+def test_clock_summary_takes_the_timed_window():
+    """NVML samples: only those inside the timed region count; reason bits are named (the idle
+    bit is not a throttle reason); with no window, every sample counts."""
+    samples = [(0.0, 1000, 0x1), (1.0, 2032, 0x0), (1.1, 2032, 0x4), (1.2, 1990, 0x0), (5.0, 800, 0x8)]
+    s = bench.clock_summary(samples, (0.9, 1.3), 2032)
+    assert s["sm_mhz"] == 2032 and s["samples"] == 3 and s["reasons"] == ["sw_power_cap"]
+    s = bench.clock_summary(samples, (None, None), 2032)
+    assert s["samples"] == 5 and s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.clock_summary([], (0, 1), 2032) is None
