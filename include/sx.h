@@ -337,7 +337,9 @@ typedef struct sx_batch_cfg {
 typedef struct sx_batch sx_batch;
 /* Build a batch: copies `items` into device memory, cuts every item into byte-balanced work
  * tiles and captures the persistent kernel into a CUDA graph.  The items' pointers must stay
- * valid while the batch is used.  Items must not write memory another item reads or writes. */
+ * valid while the batch is used.  Items must not write memory another item reads or writes.
+ * Both launch kinds run the items shortest first (fewest STREAM bytes; equal sizes in the
+ * order given), which lowers the items' mean completion time and leaves the total unchanged. */
 int sx_batch_create(sx_target *t, const sx_batch_item *items, size_t count,
                     const sx_batch_cfg *cfg, sx_batch **out);
 /* Run every item once: one graph launch on the target's stream (returns once enqueued). */
@@ -345,7 +347,7 @@ int sx_batch_launch(sx_batch *b);
 /* bulk_async_execute (Listing 2): the same launch, returning in *fut a future that completes
  * when every item has run (sx_future_wait / _test / _elapsed_ms, destroyed by the caller). */
 int sx_batch_launch_async(sx_batch *b, sx_future **fut);
-/* Baseline: run every item with its own kernel launch, in order, on the same stream. */
+/* Baseline: run every item with its own kernel launch, in the batch's order, on the same stream. */
 int sx_batch_launch_percall(sx_batch *b, const sx_launch_cfg *cfg);
 /* Completion times.  With recording on (sx_batch_set_record(b, 1), then a launch of either
  * kind), sx_batch_completion_ns gives, after that launch has completed, each item's

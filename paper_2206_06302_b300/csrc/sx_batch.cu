@@ -3,9 +3,12 @@
 //
 // The host cuts every item into work tiles of about `chunk_bytes` moved bytes (all of the item's
 // arrays counted), a multiple of 64 elements so that vector alignment is kept from tile to tile,
-// and lists the tiles item by item.  A persistent grid (SMs x blocks_per_sm) walks the list
-// round-robin: block b takes tiles b, b + grid, b + 2*grid, ...  Tiles are of equal bytes except
-// each item's last, so the static assignment balances the byte load without a work queue.
+// and lists the tiles item by item.  A batch built by sx_batch_create lists the items with the
+// fewest bytes first (shortest job first: an item's completion waits only for items no larger than
+// itself; the total work is the same in any order); the allocation-free launch keeps the caller's
+// order.  A persistent grid (SMs x blocks_per_sm) walks the list round-robin: block b takes tiles
+// b, b + grid, b + 2*grid, ...  Tiles are of equal bytes except each item's last, so the static
+// assignment balances the byte load without a work queue.
 // Inside a tile the block runs the same 16/32-byte vector loop as the VECTOR kernels, or an
 // element loop when the item's pointers do not share the vector alignment.
 //
@@ -279,6 +282,8 @@ using namespace sx;
 struct sx_batch {
     sx_target *t = nullptr;
     std::vector<sx_batch_item> items;
+    // The order items run in: fewest bytes first, ties in the caller's order (both launch kinds).
+    std::vector<uint32_t> order;
     sx_batch_cfg cfg{};
     uint64_t ntiles = 0, bytes = 0;
     DevItem *d_items = nullptr;
@@ -473,6 +478,12 @@ int build(sx_batch *b) {
     SX_TRY(fill_tables(b->items.data(), count, b->cfg.chunk_bytes, di.data(), tiles.data(), tiles.size(),
                        &nt, &b->bytes));
     b->ntiles = nt;
+    // List the tiles in the batch's run order (the tile list is item-major, so a stable sort on
+    // the item's rank keeps each item's tiles in index order).
+    std::vector<uint32_t> rank(count);
+    for (size_t k = 0; k < count; ++k) rank[b->order[k]] = (uint32_t)k;
+    std::stable_sort(tiles.begin(), tiles.begin() + nt,
+                     [&](const DevTile &l, const DevTile &r) { return rank[l.item] < rank[r.item]; });
     SX_CUDA(cudaMalloc(&b->d_items, std::max<size_t>(1, count) * sizeof(DevItem)));
     SX_CUDA(cudaMalloc(&b->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(DevTile)));
     SX_CUDA(cudaMalloc(&b->d_done, std::max<size_t>(1, count) * sizeof(uint32_t)));
@@ -718,6 +729,11 @@ int sx_batch_create(sx_target *t, const sx_batch_item *items, size_t count, cons
     if (!b) return fail(SX_ERR_OOM, "host allocation failed");
     b->t = t;
     b->items.assign(items, items + count);
+    b->order.resize(count);
+    for (size_t i = 0; i < count; ++i) b->order[i] = (uint32_t)i;
+    std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t l, uint32_t r) {
+        return item_bytes(b->items[l]) < item_bytes(b->items[r]);
+    });
     b->cfg = c;
     const int st = build(b);
     if (st != SX_OK) {
@@ -772,7 +788,8 @@ int sx_batch_launch_percall(sx_batch *b, const sx_launch_cfg *cfg) {
         if (!b->call_start) SX_CUDA(cudaEventCreate(&b->call_start));
         SX_CUDA(cudaEventRecord(b->call_start, s));
     }
-    for (size_t i = 0; i < count; ++i) {
+    for (size_t k = 0; k < count; ++k) {
+        const size_t i = b->order[k];
         const auto &it = b->items[i];
         if (it.op == SX_OP_SEED) {
             SX_TRY(launch_seed(s, it.dtype, it.out, it.n, it.seed, it.q, it.q2, it.index_base));

@@ -128,6 +128,31 @@ def test_completion_recording(target):
     sx.sx_batch_destroy(b)
 
 
+def test_items_run_shortest_first(target):
+    """Both launch kinds run the items in increasing STREAM bytes (equal sizes in the caller's
+    order).  Per call: completion times, taken in stream order, rise along that order.  One launch,
+    a grid of one block per SM walking small tiles: the smallest half of the items is done before
+    any of the ten largest (their tiles are listed ~100 grid rounds apart)."""
+    w = Workload(200, seed=14, lo_exp=8, hi_exp=20)
+    items = w.items()
+    arrays = {sx.SX_OP_COPY: 2, sx.SX_OP_SCALE: 2, sx.SX_OP_ADD: 3, sx.SX_OP_TRIAD: 3, sx.SX_OP_SEED: 1}
+    nbytes = [arrays[s["op"]] * s["n"] * np.dtype(s["dt"]).itemsize for s in w.specs]
+    order = sorted(range(len(items)), key=lambda k: nbytes[k])  # stable: ties keep the caller's order
+    b = sx.sx_batch_create(target, items, dict(chunk_bytes=16384, threads=128, blocks_per_sm=1, vec_bytes=16))
+    sx.sx_batch_set_record(b, True)
+    w.clear_outputs()
+    sx.sx_batch_launch_percall(b)
+    t = np.asarray(sx.sx_batch_completion_ns(b, len(items)), dtype=np.float64)
+    w.check("per-call, shortest first")
+    assert np.all(np.diff(t[order]) >= 0), "per-call items did not complete in the shortest-first order"
+    w.clear_outputs()
+    sx.sx_batch_launch(b)
+    t = np.asarray(sx.sx_batch_completion_ns(b, len(items)), dtype=np.float64)
+    w.check("graph, shortest first")
+    assert t[order[:100]].max() < t[order[-10:]].min()
+    sx.sx_batch_destroy(b)
+
+
 def test_empty_and_zero_length_items(target):
     b = sx.sx_batch_create(target, [])
     sx.sx_batch_launch(b)
