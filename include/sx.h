@@ -396,6 +396,19 @@ int sx_batch_run_noalloc(void *stream, const sx_batch_item *items, size_t count,
  * target, keep the fastest in the in-process table (keyed by device name, op, dtype and
  * log2(n) bucket) and return it.  *gbs = its bandwidth (STREAM byte count). */
 int sx_tune(sx_target *t, sx_op op, sx_dtype dtype, size_t n, sx_launch_cfg *best, float *gbs);
+/* Tune the four kernels of a STREAM pass together, where they run: copy c = a, scale b = q c,
+ * add c = a + b, triad a = b + q c in turn over three arrays (Section 5, Listing 4).  Each
+ * kernel starts from its shape for (op, dtype, n) (the table's entry, else the defaults); the
+ * VECTOR kernels' cache hint (0 or 1) is tried in every combination over the four, timing whole
+ * passes on scratch arrays of n elements the call allocates on the target (seeded uniform in
+ * [-1, 1) again before each trial; best of three trials).  A kernel's hint sets how much of its
+ * output is still in L2 when it ends and what the next kernel finds there, so the best hints in
+ * a pass need not be those of the kernel timed alone.  The fastest combination is stored in the
+ * table for the four (op, dtype, log2(n) bucket) entries and returned in best[0..3] (copy,
+ * scale, add, triad; may be NULL); *gbs (may be NULL) = the pass's STREAM bandwidth (10 n
+ * elements moved).  SX_ERR_INVALID for n = 0 or a NULL target, SX_ERR_DTYPE unless F32/F64,
+ * SX_ERR_OOM if three arrays of n do not fit the target's budget. */
+int sx_tune_pass(sx_target *t, sx_dtype dtype, size_t n, sx_launch_cfg *best, float *gbs);
 /* Tune the batch launch shape (chunk bytes, threads, blocks per SM, vector width) on `b`'s own
  * items (outputs are overwritten), store it for batches with a similar item mix, rebuild `b`
  * with it and return it.  *ms = device time of one launch with the best shape. */

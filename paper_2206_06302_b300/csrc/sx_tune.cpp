@@ -2,7 +2,8 @@
 // shape (the tuner's table or the caller's shape, with defaults filled in, then checked).
 //
 // For one (op, dtype, n) the tuner times candidate launch shapes of the kernel families on
-// scratch arrays and keeps the fastest.  The table is keyed by (device name, op, dtype,
+// scratch arrays and keeps the fastest; the pass tuner then times the four kernels together in
+// a STREAM pass and picks the VECTOR kernels' cache hints for that context.  The table is keyed by (device name, op, dtype,
 // floor(log2 n)) so that one measurement covers a size octave; executors with an AUTO
 // configuration look it up on every call.  Batch shapes are keyed by (device name,
 // floor(log2 mean item bytes)).  The table persists as a small JSON file.
@@ -367,6 +368,92 @@ int sx_tune(sx_target *t, sx_op op, sx_dtype dtype, size_t n, sx_launch_cfg *bes
         g_ops[OpKey{t->name, op, dtype, log2_bucket((double)n)}] = best;
     }
     if (best_out) *best_out = best;
+    if (gbs) *gbs = (float)(bytes / (best_ms * 1e-3) / 1e9);
+    return SX_OK;
+}
+
+int sx_tune_pass(sx_target *t, sx_dtype dtype, size_t n, sx_launch_cfg *best_out, float *gbs) {
+    TraceRange tr("sx_tune_pass");
+    if (!t) return fail(SX_ERR_INVALID, "target is NULL");
+    if (dtype != SX_F32 && dtype != SX_F64) return fail(SX_ERR_DTYPE, "tuner takes F32 or F64");
+    if (n == 0) return fail(SX_ERR_INVALID, "n must be positive");
+    DeviceScope ds(t->device);
+    static const int kOps[4] = {SX_OP_COPY, SX_OP_SCALE, SX_OP_ADD, SX_OP_TRIAD};
+    sx_launch_cfg base[4];
+    for (int k = 0; k < 4; ++k) {
+        base[k] = resolve_cfg(t, kOps[k], dtype, n, nullptr);
+        SX_TRY(validate_cfg(t, kOps[k], base[k]));
+    }
+    sx_array *a = nullptr, *b = nullptr, *c = nullptr;
+    int st = sx_alloc(t, dtype, n, &a);
+    if (st == SX_OK) st = sx_alloc(t, dtype, n, &b);
+    if (st == SX_OK) st = sx_alloc(t, dtype, n, &c);
+    const double bytes = 10.0 * (double)n * (double)dtype_size(dtype);
+    // passes per trial: about 8 ms of work, 2..50 (values grow 15-fold a pass; 51 FP64 passes
+    // stay finite, so the integer-unit products never meet their special-value path)
+    const double est_ms = std::max(1e-3, bytes / 6.0e9);
+    const int reps = (int)std::min(50.0, std::max(2.0, 8.0 / est_ms));
+    auto seed_all = [&]() {
+        int r = sx_seed_uniform(a, 1, -1.0, 1.0);
+        if (r == SX_OK) r = sx_seed_uniform(b, 2, -1.0, 1.0);
+        if (r == SX_OK) r = sx_seed_uniform(c, 3, -1.0, 1.0);
+        return r;
+    };
+    // one pass in Listing 4's order, as sx_stream_iter launches it
+    auto pass = [&](const sx_launch_cfg *cf) {
+        cudaStream_t s = t->stream;
+        SX_TRY(launch_stream_op(t, s, SX_OP_COPY, dtype, a->ptr, nullptr, c->ptr, n, 3.0, cf[0]));
+        SX_TRY(launch_stream_op(t, s, SX_OP_SCALE, dtype, c->ptr, nullptr, b->ptr, n, 3.0, cf[1]));
+        SX_TRY(launch_stream_op(t, s, SX_OP_ADD, dtype, a->ptr, b->ptr, c->ptr, n, 3.0, cf[2]));
+        return launch_stream_op(t, s, SX_OP_TRIAD, dtype, b->ptr, c->ptr, a->ptr, n, 3.0, cf[3]);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == SX_OK && cudaEventCreate(&e0) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "event");
+    if (st == SX_OK && cudaEventCreate(&e1) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "event");
+    sx_launch_cfg best[4];
+    std::copy(base, base + 4, best);
+    float best_ms = 1e30f;
+    for (int mask = 0; mask < 16 && st == SX_OK; ++mask) {
+        sx_launch_cfg cf[4];
+        bool dup = false;
+        for (int k = 0; k < 4; ++k) {
+            cf[k] = base[k];
+            const int h = (mask >> k) & 1;
+            if (cf[k].variant == SX_VARIANT_VECTOR) cf[k].cache_hint = h;
+            else if (h) dup = true;  // the bulk-copy families take no hint: one combination each
+        }
+        if (dup) continue;
+        float ms = 1e30f;
+        for (int trial = 0; trial < 3 && st == SX_OK; ++trial) {
+            st = seed_all();
+            if (st == SX_OK) st = pass(cf);  // warm-up, untimed
+            if (st == SX_OK && cudaEventRecord(e0, t->stream) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "event");
+            for (int r = 0; r < reps && st == SX_OK; ++r) st = pass(cf);
+            if (st == SX_OK && cudaEventRecord(e1, t->stream) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "event");
+            if (st == SX_OK && cudaEventSynchronize(e1) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "pass tuner timing");
+            float tr_ms = 0;
+            if (st == SX_OK) {
+                cudaEventElapsedTime(&tr_ms, e0, e1);
+                ms = std::min(ms, tr_ms / reps);
+            }
+        }
+        if (st == SX_OK && ms < best_ms) {
+            best_ms = ms;
+            std::copy(cf, cf + 4, best);
+        }
+    }
+    if (st == SX_OK) st = check_device_error(t);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (a) sx_free(a);
+    if (b) sx_free(b);
+    if (c) sx_free(c);
+    if (st != SX_OK) return st;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        for (int k = 0; k < 4; ++k) g_ops[OpKey{t->name, kOps[k], dtype, log2_bucket((double)n)}] = best[k];
+    }
+    if (best_out) std::copy(best, best + 4, best_out);
     if (gbs) *gbs = (float)(bytes / (best_ms * 1e-3) / 1e9);
     return SX_OK;
 }

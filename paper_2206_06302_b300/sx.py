@@ -162,6 +162,7 @@ _PROTOS = {
     "sx_batch_destroy": [P],
     "sx_batch_run_noalloc": [P, C.POINTER(sx_batch_item), SZ, C.POINTER(sx_batch_cfg)],
     "sx_tune": [P, I, I, SZ, C.POINTER(sx_launch_cfg), C.POINTER(C.c_float)],
+    "sx_tune_pass": [P, I, SZ, C.POINTER(sx_launch_cfg), C.POINTER(C.c_float)],
     "sx_tune_batch": [P, C.POINTER(sx_batch_cfg), C.POINTER(C.c_float)],
     "sx_tune_lookup": [P, I, I, SZ, C.POINTER(sx_launch_cfg)],
     "sx_tune_save": [C.c_char_p],
@@ -484,6 +485,13 @@ def sx_tune(t, op: int, dtype: int, n: int):
     c, gbs = sx_launch_cfg(), C.c_float()
     _check(lib.sx_tune(t, op, dtype, n, C.byref(c), C.byref(gbs)), "sx_tune")
     return c.as_dict(), gbs.value
+
+
+def sx_tune_pass(t, dtype: int, n: int):
+    """The four pass kernels' shapes (copy, scale, add, triad) and the pass's GB/s."""
+    c, gbs = (sx_launch_cfg * 4)(), C.c_float()
+    _check(lib.sx_tune_pass(t, dtype, n, c, C.byref(gbs)), "sx_tune_pass")
+    return [x.as_dict() for x in c], gbs.value
 
 
 def sx_tune_batch(b):

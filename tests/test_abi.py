@@ -70,6 +70,9 @@ def test_null_handles_are_rejected_without_a_gpu():
         p.sx_seed_uniform_at(None, 1, -1.0, 1.0, 5)
     assert ei.value.status == p.SX_ERR_INVALID
     with pytest.raises(p.SxError) as ei:
+        p.sx_tune_pass(None, p.SX_F64, 1 << 16)
+    assert ei.value.status == p.SX_ERR_INVALID
+    with pytest.raises(p.SxError) as ei:
         p.sx_batch_run_noalloc(None, [p.sx_batch_item(op=9, dtype=p.SX_F64, n=1)])
     assert ei.value.status == p.SX_ERR_INVALID  # refused on the host, before any CUDA call
 

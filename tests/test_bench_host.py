@@ -26,6 +26,20 @@ def test_served_summary():
     assert not s["beats_fifo"]["p99_every_load"]  # 3.0 > 2.5 at 0.9
 
 
+def test_served_summary_takes_the_median_replay():
+    """Three replays per load and mode: the summary reports the median of each figure, with every
+    replay's p99 beside it, so that one replay's outlier does not decide the comparison."""
+    runs = [dict(mode=m, offered_load=0.5, replay=r, p50_ms=p50, p99_ms=p99, **{"GB/s": 10.0})
+            for m, r, p50, p99 in (("continuous", 0, 0.1, 1.1), ("fifo", 0, 0.2, 2.1),
+                                   ("continuous", 1, 0.3, 2.9), ("fifo", 1, 0.2, 2.0),
+                                   ("continuous", 2, 0.1, 1.2), ("fifo", 2, 0.25, 2.2))]
+    s = bench.served_summary({"runs": runs, "saturation_GB/s": {"continuous": 8.0, "fifo": 5.0}})
+    ld = s["loads"]["0.5"]
+    assert ld["p99_ms"] == [1.2, 2.1] and ld["p50_ms"] == [0.1, 0.2]
+    assert ld["p99_runs_ms"] == [[1.1, 2.9, 1.2], [2.1, 2.0, 2.2]]
+    assert s["beats_fifo"]["p99_every_load"]
+
+
 def test_batched_summary():
     b = {"workload": "w", "graph_ms": 1.0, "percall_ms": 2.0, "graph_GB/s": 10.0, "percall_GB/s": 5.0,
          "speedup": 2.0, "completion_ms_p50": {"graph": 0.5, "percall": 1.0},

@@ -923,6 +923,43 @@ def test_cpp_layer_closed_form(tmp_path):
 
 
 @pytest.mark.parametrize("n", [1 << 16, 1 << 20])
+def test_pass_tuner(n):
+    """sx_tune_pass times the four kernels together in a STREAM pass: each shape it returns is the
+    kernel's starting shape (the shipped table's entry) with at most the cache hint changed, it is
+    stored under (device, op, type, log2 n) and found again by sx_tune_lookup, an AUTO executor's
+    passes (sx_stream_iter) launch with it, and three passes from seeded inputs with a ragged
+    tail equal the oracle's bit for bit."""
+    t = sx.sx_target_create(0)
+    try:
+        for dt, code in ((np.float64, sx.SX_F64), (np.float32, sx.SX_F32)):
+            e = sx.sx_executor_create(t, sx.SX_PAR)
+            start = [sx.sx_executor_resolve(e, op, code, n) for op in OPS.values()]
+            best, gbs = sx.sx_tune_pass(t, code, n)
+            assert gbs > 0
+            for k, op in enumerate(OPS.values()):
+                assert best[k]["cache_hint"] in (0, 1)
+                if start[k]["variant"] != sx.SX_VARIANT_VECTOR:
+                    assert best[k] == start[k]
+                assert {f: v for f, v in best[k].items() if f != "cache_hint"} == \
+                    {f: v for f, v in start[k].items() if f != "cache_hint"}
+                assert sx.sx_tune_lookup(t, op, code, n) == best[k]
+                assert sx.sx_executor_resolve(e, op, code, n + 37) == best[k]
+            a, b, c = si.stream_arrays(n + 37, dt, base_seed=31)
+            da, db, dc = to_device(t, a), to_device(t, b), to_device(t, c)
+            sx.sx_stream_iter(e, da, db, dc, 3.0, 3)
+            oracle.stream(a, b, c, 3.0, 3)
+            for got, want, nm in zip((da, db, dc), (a, b, c), "abc"):
+                assert_bitwise(to_host(got), want, f"pass-tuned {nm} {dt.__name__} n={n}")
+            for h in (da, db, dc):
+                sx.sx_free(h)
+            sx.sx_executor_destroy(e)
+    finally:
+        sx.sx_tune_clear()
+        sx.load_shipped_tune_table()
+        sx.sx_target_destroy(t)
+
+
+@pytest.mark.parametrize("n", [1 << 16, 1 << 20])
 def test_per_op_autotuner_search(tmp_path, n):
     """sx_tune searches the launch shapes of the three families for each of the four kernels and
     both types: the shape it returns is valid (an executor fixed to it resolves to it unchanged),
