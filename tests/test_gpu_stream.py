@@ -959,6 +959,42 @@ def test_pass_tuner(n):
         sx.sx_target_destroy(t)
 
 
+def test_pass_tuner_keeps_bulk_copy_shapes(tmp_path):
+    """A kernel whose table entry is of a bulk-copy family (no cache hint) keeps its shape through
+    sx_tune_pass, and the pass under the result still equals the oracle's bit for bit."""
+    import json
+    n = 1 << 16
+    t = sx.sx_target_create(0)
+    try:
+        path = str(tmp_path / "table.json")
+        sx.sx_tune_save(path)
+        table = json.load(open(path))
+        bulk = dict(variant=sx.SX_VARIANT_BULK, threads=256, blocks_per_sm=1, vec_bytes=0, unroll=0,
+                    cache_hint=0, tile_bytes=16384, stages=3, fp64_mul=2, reserved=0)
+        for e in table["ops"]:
+            if e["op"] == sx.SX_OP_SCALE and e["dtype"] == sx.SX_F64 and e["bucket"] == 16:
+                e.update({k: v for k, v in bulk.items() if k != "reserved"})
+        json.dump(table, open(path, "w"))
+        sx.sx_tune_load(path)
+        assert sx.sx_tune_lookup(t, sx.SX_OP_SCALE, sx.SX_F64, n) == bulk
+        best, _ = sx.sx_tune_pass(t, sx.SX_F64, n)
+        assert best[1] == bulk and sx.sx_tune_lookup(t, sx.SX_OP_SCALE, sx.SX_F64, n) == bulk
+        e = sx.sx_executor_create(t, sx.SX_PAR)
+        a, b, c = si.stream_arrays(n + 5, np.float64, base_seed=32)
+        da, db, dc = to_device(t, a), to_device(t, b), to_device(t, c)
+        sx.sx_stream_iter(e, da, db, dc, 3.0, 2)
+        oracle.stream(a, b, c, 3.0, 2)
+        for got, want, nm in zip((da, db, dc), (a, b, c), "abc"):
+            assert_bitwise(to_host(got), want, f"pass with a BULK scale: {nm}")
+        for h in (da, db, dc):
+            sx.sx_free(h)
+        sx.sx_executor_destroy(e)
+    finally:
+        sx.sx_tune_clear()
+        sx.load_shipped_tune_table()
+        sx.sx_target_destroy(t)
+
+
 @pytest.mark.parametrize("n", [1 << 16, 1 << 20])
 def test_per_op_autotuner_search(tmp_path, n):
     """sx_tune searches the launch shapes of the three families for each of the four kernels and
