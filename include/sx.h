@@ -457,6 +457,11 @@ typedef struct sx_server_cfg {
                                 inputs are computed, stored and used from registers); 1 = requests
                                 over a quarter of the step budget run in two phases, inputs first,
                                 the operation in a later piece reading them back              */
+    int32_t backlog_steps;   /* CONTINUOUS: steps launched beyond steps_in_flight while requests
+                                wait for admission (a backlog: the depth of the GPU's queue then
+                                bounds throughput and hides the host's planning time; with nobody
+                                waiting, a new arrival's first step should not queue behind more
+                                steps).  steps_in_flight + backlog_steps <= 8; 0 = 2, -1 = none */
 } sx_server_cfg;
 
 /* CONTINUOUS sharing policies.  SRPT (default): shortest remaining work first; each request in
@@ -510,6 +515,9 @@ typedef struct sx_server_stats {
                                   piece                                                     */
     uint64_t early_done;       /* CONTINUOUS: of those, DONE from the piece's own completion
                                   word, before the step holding it had completed            */
+    uint64_t steps_in_flight_peak;    /* CONTINUOUS: most steps launched and not yet completed */
+    uint64_t backlog_launches;        /* CONTINUOUS: steps launched beyond steps_in_flight
+                                         (requests were waiting for admission)               */
 } sx_server_stats;
 
 /* Start a server thread on the target (its stream carries every launch).  Thread-safe calls:

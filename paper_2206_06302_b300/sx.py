@@ -80,7 +80,7 @@ class sx_server_cfg(C.Structure):
                 ("chunk_bytes", C.c_int32), ("steps_in_flight", C.c_int32),
                 ("threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("vec_bytes", C.c_int32),
                 ("tile_bytes", C.c_int32), ("policy", C.c_int32), ("serialize_steps", C.c_int32),
-                ("split_phases", C.c_int32)]
+                ("split_phases", C.c_int32), ("backlog_steps", C.c_int32)]
 
 
 class sx_request(C.Structure):
@@ -100,7 +100,8 @@ class sx_server_stats(C.Structure):
                                           "steps", "launches", "bytes_moved", "arena_used",
                                           "arena_peak", "arena_bytes")] + [(n, C.c_double) for n in (
                                               "busy_seconds", "host_step_seconds", "host_admit_seconds")] + [
-        ("cancelled", C.c_uint64), ("fused", C.c_uint64), ("early_done", C.c_uint64)]
+        ("cancelled", C.c_uint64), ("fused", C.c_uint64), ("early_done", C.c_uint64),
+        ("steps_in_flight_peak", C.c_uint64), ("backlog_launches", C.c_uint64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -231,9 +231,46 @@ def test_short_requests_overtake_a_long_one(target):
     assert order[sx.SX_SERVE_FIFO][0] == 0, order
 
 
+@pytest.mark.parametrize("backlog", [0, -1])
+def test_backlog_steps_only_while_requests_wait(target, backlog):
+    """Two slots for six requests, so that four wait for admission: with the default backlog the
+    server keeps up to steps_in_flight + 2 steps on the GPU while they wait (each step here runs
+    ~45 us, much longer than planning one), with backlog_steps = -1 at most steps_in_flight; the
+    results equal the oracle's either way."""
+    reqs = [dict(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=1 << 24, q=3.0, seed_x=40 + k, seed_y=50 + k,
+                 lo=-1.0, hi=1.0) for k in range(6)]
+    s = sx.sx_server_create(target, budget_bytes=2 << 30, max_active=2, chunk_bytes=256 << 20,
+                            steps_in_flight=2, backlog_steps=backlog)
+    ids = [sx.sx_server_submit(s, **r) for r in reqs]
+    _check_all(s, ids, reqs, f"backlog {backlog}")
+    st = sx.sx_server_stats_get(s)
+    sx.sx_server_destroy(s)
+    if backlog == -1:
+        assert st["steps_in_flight_peak"] <= 2 and st["backlog_launches"] == 0, st
+    else:
+        assert 3 <= st["steps_in_flight_peak"] <= 4 and st["backlog_launches"] >= 1, st
+
+
+def test_a_lone_request_gets_no_backlog_steps(target):
+    """Nothing waits for admission: however long the request, at most steps_in_flight steps."""
+    r = dict(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=1 << 24, q=3.0, seed_x=60, seed_y=61, lo=-1.0, hi=1.0)
+    s = sx.sx_server_create(target, budget_bytes=1 << 30, chunk_bytes=64 << 20)
+    ids = [sx.sx_server_submit(s, **r)]
+    _check_all(s, ids, [r], "lone request")
+    st = sx.sx_server_stats_get(s)
+    sx.sx_server_destroy(s)
+    assert st["steps"] >= 8 and st["steps_in_flight_peak"] <= 2 and st["backlog_launches"] == 0, st
+
+
 def test_bad_calls(target):
     with pytest.raises(sx.SxError):
         sx.sx_server_create(target, budget_bytes=0)
+    for kw in (dict(steps_in_flight=8, backlog_steps=1), dict(backlog_steps=-2), dict(steps_in_flight=6, backlog_steps=3)):
+        with pytest.raises(sx.SxError) as ei:
+            sx.sx_server_create(target, budget_bytes=1 << 20, **kw)
+        assert ei.value.status == sx.SX_ERR_INVALID, kw
+    s = sx.sx_server_create(target, budget_bytes=1 << 20, steps_in_flight=8)  # no room left: no backlog
+    sx.sx_server_destroy(s)
     s = sx.sx_server_create(target, budget_bytes=1 << 20)
     with pytest.raises(sx.SxError) as ei:
         sx.sx_server_submit(s, op=7, dtype=sx.SX_F64, n=10)
