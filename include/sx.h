@@ -391,6 +391,10 @@ int sx_batch_destroy(sx_batch *b);
 int sx_batch_run_noalloc(void *stream, const sx_batch_item *items, size_t count, const sx_batch_cfg *cfg);
 
 /* ---- autotuner ------------------------------------------------------------------------ */
+/* The tuners time launches on the target's stream with CUDA events: other work on the same GPU
+ * at the same time skews which shape wins (never the results computed under it).  sx_tune and
+ * sx_tune_pass allocate scratch arrays on the target and free them before returning;
+ * sx_tune_batch runs the batch's own items. */
 /* Time the candidate launch shapes (the three families, vector widths, unroll, block counts,
  * cache hints, bulk tile sizes and pipeline depths) for (op, dtype, n) on scratch arrays the tuner allocates on the
  * target, keep the fastest in the in-process table (keyed by device name, op, dtype and
