@@ -326,7 +326,10 @@ typedef struct sx_batch_item {
 
 /* Launch shape of a batch.  chunk_bytes: bytes moved per work tile (all arrays), the unit a
  * block takes at a time (16 KiB..8 MiB); threads per block; blocks_per_sm of the persistent
- * grid; vec_bytes 16/32.  Zero fields = default (autotuned values if sx_tune_batch ran). */
+ * grid, capped at the blocks of that size an SM holds at once (the grid walks its tiles
+ * round-robin, which assumes every block is resident); vec_bytes 16/32.  Zero fields = the
+ * values sx_tune_batch stored for a similar item mix, else 512 KiB tiles, 512 threads, 2 blocks
+ * per SM, 32-byte vectors. */
 typedef struct sx_batch_cfg {
     int32_t chunk_bytes;
     int32_t threads;

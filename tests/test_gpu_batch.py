@@ -153,6 +153,48 @@ def test_items_run_shortest_first(target):
     sx.sx_batch_destroy(b)
 
 
+def test_first_round_runs_first_whatever_blocks_per_sm_asks(target):
+    """The persistent grid is capped at the blocks the SMs hold at once: with 2500 one-tile items
+    ahead of four large ones and a shape asking for more blocks than fit (128 threads x 16 per SM),
+    every small item is done within the first rounds, early in the launch.  (A block left waiting
+    for a free SM starts only when a resident block has finished all of its tiles, so the small
+    items it owns would be done about halfway through.)  The results equal the oracle's."""
+    import torch
+    rng = np.random.default_rng(15)
+    small = [256] * 2500
+    large = [1 << 22] * 4
+    lens = small + large
+    offs, total = [], 0
+    for n in lens:
+        r = []
+        for _ in range(3):
+            total = (total + 255) // 256 * 256
+            r.append(total)
+            total += n * 8
+        offs.append(r)
+    buf = torch.zeros(total, dtype=torch.uint8, device="cuda")
+    base = buf.data_ptr()
+    host = []
+    for n, o in zip(lens, offs):
+        x, y = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+        host.append((x, y))
+        buf[o[0]:o[0] + 8 * n] = torch.from_numpy(x.view(np.uint8)).cuda()
+        buf[o[1]:o[1] + 8 * n] = torch.from_numpy(y.view(np.uint8)).cuda()
+    items = [sx.sx_batch_item(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=n, x=base + o[0], y=base + o[1],
+                              out=base + o[2], q=3.0) for n, o in zip(lens, offs)]
+    b = sx.sx_batch_create(target, items, dict(chunk_bytes=16384, threads=128, blocks_per_sm=16, vec_bytes=32))
+    sx.sx_batch_set_record(b, True)
+    sx.sx_batch_launch(b)
+    t = np.asarray(sx.sx_batch_completion_ns(b, len(items)), dtype=np.float64)
+    assert t[:2500].max() < 0.25 * t.max(), (t[:2500].max(), t.max())
+    h = buf.cpu().numpy()
+    for k in list(range(0, 2500, 97)) + [2500, 2503]:
+        n, o = lens[k], offs[k]
+        got = h[o[2]:o[2] + 8 * n].view(np.float64)
+        assert_bitwise(got, oracle.apply("triad", host[k][0], host[k][1], 3.0), f"item {k}")
+    sx.sx_batch_destroy(b)
+
+
 def test_empty_and_zero_length_items(target):
     b = sx.sx_batch_create(target, [])
     sx.sx_batch_launch(b)
