@@ -328,7 +328,7 @@ typedef struct sx_batch_item {
  * block takes at a time (16 KiB..8 MiB); threads per block; blocks_per_sm of the persistent
  * grid, capped at the blocks of that size an SM holds at once (the grid walks its tiles
  * round-robin, which assumes every block is resident); vec_bytes 16/32.  Zero fields = the
- * values sx_tune_batch stored for a similar item mix, else 512 KiB tiles, 512 threads, 2 blocks
+ * values sx_tune_batch stored for a similar item mix, else 512 KiB tiles, 128 threads, 7 blocks
  * per SM, 32-byte vectors. */
 typedef struct sx_batch_cfg {
     int32_t chunk_bytes;

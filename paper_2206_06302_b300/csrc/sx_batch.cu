@@ -363,10 +363,10 @@ sx_batch_cfg resolve_batch_cfg(const sx_target *t, const sx_batch_item *items, s
         c = *req;
     }
     // the fastest shape measured on the 4096-instance FP64 batch among those whose blocks are all
-    // resident at once (the kernel's 54 registers allow 36 warps per SM)
+    // resident at once (the kernel's 54 registers allow 36 warps per SM; 28 ran fastest)
     if (c.chunk_bytes == 0) c.chunk_bytes = 512 * 1024;
-    if (c.threads == 0) c.threads = 512;
-    if (c.blocks_per_sm == 0) c.blocks_per_sm = 2;
+    if (c.threads == 0) c.threads = 128;
+    if (c.blocks_per_sm == 0) c.blocks_per_sm = 7;
     if (c.vec_bytes == 0) c.vec_bytes = 32;
     return c;
 }
@@ -901,7 +901,9 @@ int sx_tune_batch(sx_batch *b, sx_batch_cfg *best_out, float *ms_out) {
     cudaEvent_t e0, e1;
     SX_CUDA(cudaEventCreate(&e0));
     SX_CUDA(cudaEventCreate(&e1));
-    auto time_cfg = [&](const sx_batch_cfg &c, float *ms) -> int {
+    auto time_cfg = [&](sx_batch_cfg &c, float *ms) -> int {
+        // blocks beyond those an SM holds are capped at launch: record the shape that runs
+        c.blocks_per_sm = std::min(c.blocks_per_sm, resident_blocks(batch_kernel(c.vec_bytes), c.threads));
         b->cfg = c;
         SX_TRY(build(b));
         SX_CUDA(cudaGraphLaunch(b->exec, s));  // warm
@@ -921,29 +923,45 @@ int sx_tune_batch(sx_batch *b, sx_batch_cfg *best_out, float *ms_out) {
     sx_batch_cfg best = b->cfg;
     float best_ms = 1e30f;
     int st = SX_OK;
-    // pass 1: tile size x residency; pass 2: block size and vector width at the best of pass 1
-    for (int chunk : {64 << 10, 128 << 10, 256 << 10, 512 << 10, 1 << 20, 2 << 20})
-        for (int bps : {1, 2, 4, 8}) {
-            sx_batch_cfg c{chunk, 256, bps, 32};
-            float ms = 0;
-            st = time_cfg(c, &ms);
-            if (st != SX_OK) break;
-            if (ms < best_ms) best_ms = ms, best = c;
+    auto try_cfg = [&](sx_batch_cfg c) -> int {
+        if (validate_batch_cfg(c) != SX_OK) {
+            clear_error();
+            return SX_OK;
         }
+        float ms = 0;
+        SX_TRY(time_cfg(c, &ms));
+        if (ms < best_ms) best_ms = ms, best = c;
+        return SX_OK;
+    };
+    // pass 1: tile size x residency; pass 2: block size and vector width at the best of pass 1
+    // (same threads per SM); pass 3: blocks per SM from 1 to all an SM holds, for blocks of 64 to
+    // 512 threads (on the 4096-instance FP64 batch 28 warps per SM ran 2-4% faster than 32 or 36,
+    // and 36 is all the kernel's registers allow); pass 4: the tile size again at that shape
+    for (int chunk : {64 << 10, 128 << 10, 256 << 10, 512 << 10, 1 << 20, 2 << 20})
+        for (int bps : {1, 2, 4, 8})
+            if (st == SX_OK) st = try_cfg(sx_batch_cfg{chunk, 256, bps, 32});
     if (st == SX_OK) {
         const sx_batch_cfg p1 = best;
-        for (int th : {128, 256, 512, 1024})
-            for (int vb : {16, 32}) {
-                sx_batch_cfg c{p1.chunk_bytes, th, std::max(1, std::min(p1.blocks_per_sm * 256 / th, 2048 / th)), vb};
-                if (validate_batch_cfg(c) != SX_OK) {
-                    clear_error();
-                    continue;
-                }
-                float ms = 0;
-                st = time_cfg(c, &ms);
-                if (st != SX_OK) break;
-                if (ms < best_ms) best_ms = ms, best = c;
-            }
+        for (int th : {64, 128, 256, 512, 1024})
+            for (int vb : {16, 32})
+                if (st == SX_OK)
+                    st = try_cfg(sx_batch_cfg{p1.chunk_bytes, th,
+                                              std::max(1, std::min(p1.blocks_per_sm * 256 / th, 2048 / th)), vb});
+    }
+    if (st == SX_OK) {
+        const sx_batch_cfg p2 = best;
+        for (int th : {64, 128, 256, 512}) {
+            const int most = std::min(resident_blocks(batch_kernel(p2.vec_bytes), th), 2048 / th);
+            for (int bps = 1; bps <= most && st == SX_OK; ++bps)
+                if (th != p2.threads || bps != p2.blocks_per_sm)
+                    st = try_cfg(sx_batch_cfg{p2.chunk_bytes, th, bps, p2.vec_bytes});
+        }
+    }
+    if (st == SX_OK) {
+        const sx_batch_cfg p3 = best;
+        for (int chunk : {64 << 10, 128 << 10, 256 << 10, 512 << 10, 1 << 20, 2 << 20})
+            if (chunk != p3.chunk_bytes && st == SX_OK)
+                st = try_cfg(sx_batch_cfg{chunk, p3.threads, p3.blocks_per_sm, p3.vec_bytes});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
