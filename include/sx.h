@@ -357,7 +357,8 @@ int sx_batch_launch_percall(sx_batch *b, const sx_launch_cfg *cfg);
  * completion time in ns of the device global timer relative to the launch's first work. */
 int sx_batch_set_record(sx_batch *b, int record);
 int sx_batch_completion_ns(sx_batch *b, uint64_t *t_ns, size_t count);
-/* The batch's launch shape, number of work tiles and STREAM bytes of one launch. */
+/* The batch's launch shape (as it runs: blocks per SM capped at those an SM holds), number of
+ * work tiles and STREAM bytes of one launch. */
 int sx_batch_info(const sx_batch *b, sx_batch_cfg *cfg, uint64_t *tiles, uint64_t *bytes);
 /* Wait for the target's stream, then free the batch's graph and tables. */
 int sx_batch_destroy(sx_batch *b);

@@ -759,9 +759,11 @@ int sx_batch_create(sx_target *t, const sx_batch_item *items, size_t count, cons
     *out = nullptr;
     if (count > 0xffffffffull) return fail(SX_ERR_INVALID, "too many items");
     SX_TRY(check_items(items, count));
-    const sx_batch_cfg c = resolve_batch_cfg(t, items, count, cfg);
+    sx_batch_cfg c = resolve_batch_cfg(t, items, count, cfg);
     SX_TRY(validate_batch_cfg(c));
     DeviceScope ds(t->device);
+    // the shape that runs (sx_batch_info reports it): no more blocks per SM than an SM holds
+    c.blocks_per_sm = std::min(c.blocks_per_sm, resident_blocks(batch_kernel(c.vec_bytes), c.threads));
     sx_batch *b = new (std::nothrow) sx_batch();
     if (!b) return fail(SX_ERR_OOM, "host allocation failed");
     b->t = t;

@@ -183,6 +183,8 @@ def test_first_round_runs_first_whatever_blocks_per_sm_asks(target):
     items = [sx.sx_batch_item(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=n, x=base + o[0], y=base + o[1],
                               out=base + o[2], q=3.0) for n, o in zip(lens, offs)]
     b = sx.sx_batch_create(target, items, dict(chunk_bytes=16384, threads=128, blocks_per_sm=16, vec_bytes=32))
+    cfg, _, _ = sx.sx_batch_info(b)
+    assert 1 <= cfg["blocks_per_sm"] < 16 and cfg["threads"] == 128  # as it runs: capped
     sx.sx_batch_set_record(b, True)
     sx.sx_batch_launch(b)
     t = np.asarray(sx.sx_batch_completion_ns(b, len(items)), dtype=np.float64)
