@@ -454,8 +454,8 @@ typedef struct sx_server_cfg {
     int32_t max_active;      /* requests admitted at once (slots), 1..65536; 0 = 256          */
     int32_t chunk_bytes;     /* CONTINUOUS: byte budget of one step (1 MiB..2 GiB); 0 = 1 GiB   */
     int32_t steps_in_flight; /* CONTINUOUS: launched steps not yet completed (1..8); 0 = 2    */
-    int32_t threads, blocks_per_sm, vec_bytes;  /* batched-kernel shape; 0 = 256, 4, 32     */
-    int32_t tile_bytes;      /* CONTINUOUS: work-tile bytes of the batched kernel; 0 = 128 KiB */
+    int32_t threads, blocks_per_sm, vec_bytes;  /* batched-kernel shape; 0 = 128, 8, 32     */
+    int32_t tile_bytes;      /* CONTINUOUS: work-tile bytes of the batched kernel; 0 = 256 KiB */
     int32_t policy;          /* CONTINUOUS: how a step's budget is shared, SX_SERVE_POLICY_*  */
     int32_t serialize_steps; /* CONTINUOUS: 0 = a step may start while the previous one ends
                                 (programmatic dependent launch; pieces that need the previous
