@@ -168,6 +168,9 @@ class NvmlReader:
             raise OSError("NVML reasons query failed")
         return v.value
 
+    def close(self):
+        self.lib.nvmlShutdown()
+
 
 class ClockSampler:
     """SM clocks and throttle reasons during the timed region: NVML read every 2 ms by a thread
@@ -184,6 +187,7 @@ class ClockSampler:
         self.nvml_samples, self.window, self.nvml_max = [], [None, None], None
         self._stop = False
         self._thread = None
+        self._nvml = None
 
     def _poll_nvml(self, nvml):
         while not self._stop:
@@ -194,7 +198,7 @@ class ClockSampler:
             time.sleep(0.002)
 
     def __enter__(self):
-        nvml = NvmlReader.open(self.device)
+        nvml = self._nvml = NvmlReader.open(self.device)
         if nvml is not None:
             import threading
             self.nvml_max = nvml.sm_max_mhz()
@@ -222,6 +226,8 @@ class ClockSampler:
         self._stop = True
         if self._thread is not None:
             self._thread.join(timeout=1)
+        if self._nvml is not None and (self._thread is None or not self._thread.is_alive()):
+            self._nvml.close()
         if self.proc is not None:
             self.proc.terminate()
             try:
