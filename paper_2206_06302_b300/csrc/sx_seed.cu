@@ -13,16 +13,38 @@ using namespace dev;
 
 // ---- seeded bulk construction ---------------------------------------------------------------
 // All threads of the grid share the range (seed_range); PM1: lo = -1, hi = 1 in binary64.
+// Blocks of 256 threads that one SM holds at once: the bounds make the compiler keep each form's
+// registers within them (the binary64 [-1, 1) form needs 38 registers: 6 blocks; the others fit
+// 32: 8), and the grid-stride loop launches no more than that, so that no block waits for
+// another to finish before it starts (such blocks would run the loop's last share alone).
+template <class T, bool PM1>
+constexpr int seed_blocks_per_sm() { return (sizeof(T) == 8 && PM1) ? 6 : 8; }
+
 template <class T, bool PM1, int MV = 0>
-__global__ void __launch_bounds__(256) k_seed(T *out, uint64_t n, uint64_t seed, T lo, T span, uint64_t base) {
+__global__ void __launch_bounds__(256, seed_blocks_per_sm<T, PM1>())
+    k_seed(T *out, uint64_t n, uint64_t seed, T lo, T span, uint64_t base) {
     seed_range<T, PM1, MV>(out, n, seed, base, lo, span, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                            (uint64_t)gridDim.x * blockDim.x);
 }
 
-// Blocks of 256 threads for `n` elements taken `per_thread` at a time: up to 8 per SM.
-unsigned seed_blocks(size_t n, int per_thread) {
+// Blocks of 256 threads for `n` elements taken `per_thread` at a time: at most `per_sm` per SM of
+// the current device.
+unsigned seed_blocks(size_t n, int per_thread, int per_sm) {
+    static std::atomic<int> sms[64];  // per device, 0 until first asked
+    int dev = 0;
+    cudaGetDevice(&dev);
+    uint64_t nsm = 148;
+    if (dev >= 0 && dev < 64) {
+        int v = sms[dev].load(std::memory_order_relaxed);
+        if (v == 0) {
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+            if (v <= 0) v = 148;
+            sms[dev].store(v, std::memory_order_relaxed);
+        }
+        nsm = (uint64_t)v;
+    }
     uint64_t b = (n + 256ull * per_thread - 1) / (256ull * per_thread);
-    if (b > 148ull * 8) b = 148ull * 8;
+    if (b > nsm * per_sm) b = nsm * per_sm;
     return b == 0 ? 1u : (unsigned)b;
 }
 
@@ -98,12 +120,13 @@ int launch_seed(cudaStream_t s, int dtype, void *out, size_t n, uint64_t seed, d
     if (n == 0) return SX_OK;
     if (dtype == SX_F64) {
         const double span = hi - lo;
-        const unsigned b = seed_blocks(n, 8);
+        const unsigned b = seed_blocks(n, 8, seed_blocks_per_sm<double, false>());
+        const unsigned b_pm1 = seed_blocks(n, 8, seed_blocks_per_sm<double, true>());
         // general range: most products on the integer units (not for a zero, subnormal, infinite
         // or NaN span, which the integer product would only send back to the FP64 pipe)
         const int mv = mul_variant(1, span);
         if (lo == -1.0 && hi == 1.0)
-            k_seed<double, true><<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
+            k_seed<double, true><<<b_pm1, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
         else if (mv == 3)
             k_seed<double, false, 3><<<b, 256, 0, s>>>((double *)out, n, seed, lo, span, index_base);
         else if (mv == 1)
@@ -113,7 +136,8 @@ int launch_seed(cudaStream_t s, int dtype, void *out, size_t n, uint64_t seed, d
     } else if (dtype == SX_F32) {
         const float lo32 = (float)lo, hi32 = (float)hi;
         const float span = hi32 - lo32;
-        k_seed<float, false><<<seed_blocks(n, 16), 256, 0, s>>>((float *)out, n, seed, lo32, span, index_base);
+        k_seed<float, false><<<seed_blocks(n, 16, seed_blocks_per_sm<float, false>()), 256, 0, s>>>(
+            (float *)out, n, seed, lo32, span, index_base);
     } else {
         return fail(SX_ERR_DTYPE, "seed_uniform takes F32 or F64 (got dtype %d)", dtype);
     }
