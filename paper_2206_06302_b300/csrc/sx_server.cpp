@@ -724,6 +724,10 @@ int sx_server_create(sx_target *t, const sx_server_cfg *cfg, sx_server **out) {
     if (c.mode != SX_SERVE_CONTINUOUS && c.mode != SX_SERVE_FIFO) return fail(SX_ERR_INVALID, "mode %d", c.mode);
     if (c.budget_bytes == 0) return fail(SX_ERR_INVALID, "budget_bytes must be positive");
     if (c.max_active == 0) c.max_active = 256;
+    // step budget: 1 GiB of STREAM bytes (~110 us of GPU time at saturation); on the served
+    // workload, alternating in one process, 768 MiB gave 2-4% lower p99 at 0.8 and 0.95 load but
+    // 2.8% less throughput at saturation, 512 MiB a lower and noisier saturation, 2 GiB a higher
+    // p50 at 0.95 load
     if (c.chunk_bytes == 0) c.chunk_bytes = 1 << 30;
     if (c.steps_in_flight == 0) c.steps_in_flight = 2;
     if (c.policy != SX_SERVE_POLICY_SHORT_FIRST && c.policy != SX_SERVE_POLICY_FAIR &&
