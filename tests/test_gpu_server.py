@@ -231,18 +231,20 @@ def test_short_requests_overtake_a_long_one(target):
     assert order[sx.SX_SERVE_FIFO][0] == 0, order
 
 
+@pytest.mark.parametrize("split", [0, 1])
 @pytest.mark.parametrize("backlog", [0, -1])
-def test_backlog_steps_only_while_requests_wait(target, backlog):
+def test_backlog_steps_only_while_requests_wait(target, backlog, split):
     """Two slots for six requests, so that four wait for admission: with the default backlog the
     server keeps up to steps_in_flight + 2 steps on the GPU while they wait (each step here runs
     ~45 us, much longer than planning one), with backlog_steps = -1 at most steps_in_flight; the
-    results equal the oracle's either way."""
+    results equal the oracle's either way.  With split phases the operation pieces wait on the
+    device for inputs built by steps still in flight, up to three steps back."""
     reqs = [dict(op=sx.SX_OP_TRIAD, dtype=sx.SX_F64, n=1 << 24, q=3.0, seed_x=40 + k, seed_y=50 + k,
                  lo=-1.0, hi=1.0) for k in range(6)]
     s = sx.sx_server_create(target, budget_bytes=2 << 30, max_active=2, chunk_bytes=256 << 20,
-                            steps_in_flight=2, backlog_steps=backlog)
+                            steps_in_flight=2, backlog_steps=backlog, split_phases=split)
     ids = [sx.sx_server_submit(s, **r) for r in reqs]
-    _check_all(s, ids, reqs, f"backlog {backlog}")
+    _check_all(s, ids, reqs, f"backlog {backlog} split {split}")
     st = sx.sx_server_stats_get(s)
     sx.sx_server_destroy(s)
     if backlog == -1:
