@@ -584,10 +584,12 @@ def served_summary(s):
     sat = s["saturation_GB/s"]
     return {"what": "continuous batching vs per-call FIFO; per load [continuous, fifo]; GB/s in STREAM bytes "
                     "(input construction and operation); continuous_split_phases: batching without the "
-                    "construct-then-operate pieces",
+                    "construct-then-operate pieces; *_dram_*: the DRAM traffic each mode moves for that work "
+                    "(continuous reads no input back)",
             "saturation_GB/s": sat, "saturation_runs_GB/s": s.get("saturation_runs_GB/s"),
             "saturation_frac_measured": s.get("saturation_frac_measured"),
             "saturation_dram_GB/s": s.get("saturation_dram_GB/s"),
+            "saturation_dram_frac_measured": s.get("saturation_dram_frac_measured"),
             "saturation_gain": round(sat["continuous"] / sat["fifo"], 4) if sat.get("fifo") else None,
             "saturation_gain_worst_run": (round(min(s["saturation_runs_GB/s"]["continuous"]) /
                                                 max(s["saturation_runs_GB/s"]["fifo"]), 4)
@@ -697,6 +699,8 @@ def served_section(sx, torch, t, stream, args, rank):
         # requests run fused and the others read their inputs back, between the two)
         if name in dram:
             out.setdefault("saturation_dram_GB/s", {})[name] = round(max(runs) * dram[name] / sum(nbytes), 1)
+            out.setdefault("saturation_dram_frac_measured", {})[name] = round(
+                max(runs) * dram[name] / sum(nbytes) / _measured_peaks()[0], 4)
     out["dram_bytes_per_stream_byte"] = {k: round(v / sum(nbytes), 4) for k, v in dram.items()}
     capacity = out["saturation_GB/s"]["fifo"] * 1e9
     out["capacity_from"] = "per-call FIFO throughput at saturation"
