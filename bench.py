@@ -449,6 +449,17 @@ def batched_section(sx, torch, t, stream, args, rank):
 
     g_ms = timed(lambda: sx.sx_batch_launch(b), args.batch_reps)
     p_ms = timed(lambda: sx.sx_batch_launch_percall(b), max(3, args.batch_reps // 2))
+    # the same per-call launches captured once into a CUDA graph and replayed: one kernel node per
+    # instance without the host's cost per launch, the strongest form of one launch per instance
+    pcg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(pcg, stream=stream, capture_error_mode="thread_local"):
+        sx.sx_batch_launch_percall(b)
+
+    def replay_percall():  # on the target's stream (a replay goes to torch's current stream)
+        with torch.cuda.stream(stream):
+            pcg.replay()
+
+    pg_ms = timed(replay_percall, max(3, args.batch_reps // 2))
     # the same items through the entry point that allocates nothing (tiles of at least 1 MiB, so
     # the workload's tiles fit its static table): device time, and the host time of each call when
     # calls are enqueued back to back, beside that of a graph launch
@@ -506,13 +517,19 @@ def batched_section(sx, torch, t, stream, args, rank):
     sx.sx_batch_run_noalloc(stream.cuda_stream, items, na_cfg)
     sx.sx_target_synchronize(t)
     after_noalloc = snapshot(2)
-    same = all(np.array_equal(g, p) for g, p in zip(after_graph, after_percall))
+    poison()
+    replay_percall()
+    torch.cuda.synchronize()
+    after_percall_graph = snapshot(2)
+    del pcg
+    same = all(np.array_equal(g, p) for g, p in zip(after_graph, after_percall)) and \
+        all(np.array_equal(g, p) for g, p in zip(after_graph, after_percall_graph))
     same_noalloc = all(np.array_equal(g, p) for g, p in zip(after_graph, after_noalloc))
     inputs_ok = all(np.array_equal(h, si.uniform(si.array_seed(si.BASE_SEED, 0, first + k), inst[k][1], np.float64)
                                    .view(np.uint64)) for k, h in zip(spot, snapshot(0)))
     sx.sx_batch_destroy(b)
     sx.sx_free(buf)
-    gm, pm = g_ms[len(g_ms) // 2], p_ms[len(p_ms) // 2]
+    gm, pm, pgm = g_ms[len(g_ms) // 2], p_ms[len(p_ms) // 2], pg_ms[len(pg_ms) // 2]
     return {
         "share": (f"instances [{first}, {first + len(inst)}) of {args.batch_count}, assigned whole to this rank"
                   if args.shard else "all instances"),
@@ -523,9 +540,11 @@ def batched_section(sx, torch, t, stream, args, rank):
         "graph_frac_measured": round(nbytes / (gm * 1e-3) / 1e9 / _measured_peaks()[0], 4),
         "percall_ms": round(pm, 4), "percall_GB/s": round(nbytes / (pm * 1e-3) / 1e9, 1),
         "speedup": round(pm / gm, 3),
+        "percall_graph_ms": round(pgm, 4), "percall_graph_GB/s": round(nbytes / (pgm * 1e-3) / 1e9, 1),
+        "speedup_vs_percall_graph": round(pgm / gm, 3),
         "completion_ms_p50": {"graph": round(_pct(comp_g, 50), 4), "percall": round(_pct(comp_p, 50), 4)},
         "completion_ms_p99": {"graph": round(_pct(comp_g, 99), 4), "percall": round(_pct(comp_p, 99), 4)},
-        "launches": {"graph": 1, "percall": len(items)},
+        "launches": {"graph": 1, "percall": len(items), "percall_graph": f"1 graph of {len(items)} kernel nodes"},
         "graph_equals_percall_8_instances": same, "inputs_match_generator_8_instances": inputs_ok,
         "noalloc": {"what": "sx_batch_run_noalloc on the same items, calls enqueued back to back",
                     "cfg": na_cfg, "device_ms": round(na_ms[len(na_ms) // 2], 4),
@@ -537,18 +556,23 @@ def batched_section(sx, torch, t, stream, args, rank):
 
 def batched_summary(b):
     """The batched comparison in a few hundred bytes: one graph launch vs one launch per instance
-    (device time, STREAM bytes per second, per-instance completion p50/p99) and whether the
+    (enqueued one by one, and replayed from a graph of per-instance kernel nodes: device time,
+    STREAM bytes per second; per-instance completion p50/p99 of the first two) and whether the
     graph launch beats the per-call launches on throughput and on p99."""
     p50, p99 = b["completion_ms_p50"], b["completion_ms_p99"]
     return {"what": b["workload"],
-            "ms": {"graph": b["graph_ms"], "percall": b["percall_ms"]},
-            "GB/s": {"graph": b["graph_GB/s"], "percall": b["percall_GB/s"]},
-            "speedup": b["speedup"], "p50_ms": p50, "p99_ms": p99,
+            "ms": {"graph": b["graph_ms"], "percall": b["percall_ms"], "percall_graph": b.get("percall_graph_ms")},
+            "GB/s": {"graph": b["graph_GB/s"], "percall": b["percall_GB/s"],
+                     "percall_graph": b.get("percall_graph_GB/s")},
+            "speedup": b["speedup"], "speedup_vs_percall_graph": b.get("speedup_vs_percall_graph"),
+            "p50_ms": p50, "p99_ms": p99,
             "bit_identical_8_instances": b["graph_equals_percall_8_instances"],
             "noalloc_ms": b["noalloc"]["device_ms"],
             "noalloc_host_us_per_call": b["noalloc"]["host_us_per_call_median"],
             "graph_launch_host_us": b["noalloc"]["graph_launch_host_us_median"],
             "beats_percall": {"throughput": b["graph_GB/s"] > b["percall_GB/s"],
+                              "throughput_vs_percall_graph": (b["graph_GB/s"] > b["percall_graph_GB/s"]
+                                                              if b.get("percall_graph_GB/s") else None),
                               "p99": p99["graph"] < p99["percall"]}}
 
 

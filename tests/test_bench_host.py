@@ -42,11 +42,13 @@ def test_served_summary_takes_the_median_replay():
 
 def test_batched_summary():
     b = {"workload": "w", "graph_ms": 1.0, "percall_ms": 2.0, "graph_GB/s": 10.0, "percall_GB/s": 5.0,
+         "percall_graph_ms": 1.5, "percall_graph_GB/s": 6.7, "speedup_vs_percall_graph": 1.5,
          "speedup": 2.0, "completion_ms_p50": {"graph": 0.5, "percall": 1.0},
          "completion_ms_p99": {"graph": 0.9, "percall": 1.9}, "graph_equals_percall_8_instances": True,
          "noalloc": {"device_ms": 1.1, "host_us_per_call_median": 900.0, "graph_launch_host_us_median": 2.0}}
     s = bench.batched_summary(b)
-    assert s["beats_percall"] == {"throughput": True, "p99": True} and s["noalloc_host_us_per_call"] == 900.0
+    assert s["beats_percall"] == {"throughput": True, "throughput_vs_percall_graph": True, "p99": True}
+    assert s["noalloc_host_us_per_call"] == 900.0 and s["ms"]["percall_graph"] == 1.5
 
 
 def test_served_workload_byte_accounting():
